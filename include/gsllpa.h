@@ -1,0 +1,206 @@
+/*
+ * gsllpa.h -- C ABI of the GB300 (sm_103a) GSL-LPA library.
+ *
+ * GSL-LPA (arXiv 2403.01261) is label-propagation community detection
+ * followed by a split-last step that relabels every community into its
+ * internally connected pieces.  This library runs both phases, and the
+ * modularity score, as CUDA kernels on one GPU.
+ *
+ * Graph.  An undirected graph G(V, E, w) (Section 3, "Preliminaries") is
+ * passed as symmetric CSR: every edge {i, j} is stored twice, as (i, j) in
+ * row i and (j, i) in row j, with equal weights.  Symmetry is required but
+ * not checked.  Rows need not be sorted; a repeated entry adds its weight
+ * once per occurrence.
+ *
+ * Memory.  Unless a name ends in _host, every pointer argument that refers
+ * to graph or label data is a DEVICE pointer on the context's device, owned
+ * by the caller, and must stay valid until the call has completed on its
+ * stream.  Scratch memory (label double buffers, frontier flags, worklists,
+ * hash tables, union-find parents) is owned by the context, grown on demand
+ * and reused across calls.  A context is not thread safe: use one per host
+ * thread.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL: the legacy
+ * default stream).  Work is queued on that stream and every entry point
+ * synchronises it before returning: the sweep loop reads the change count
+ * back after every sweep (the stop test of Algorithm 3 needs it) and all
+ * calls report device-detected input errors through their return code.
+ *
+ * Errors.  Every entry point returns GSL_OK (0) or one of the GSL_ERR_*
+ * codes below; gsl_strerror() names them and gsl_ctx_last_error() returns a
+ * one-line detail for the last failing call on a context.  On error the
+ * contents of output buffers are unspecified.
+ */
+#ifndef GSLLPA_H
+#define GSLLPA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSL_OK 0
+#define GSL_ERR_INVALID 1   /* bad argument or malformed graph / labels          */
+#define GSL_ERR_OVERFLOW 2  /* a weighted degree (sum of a row's weights) >= 2^31 */
+#define GSL_ERR_NOMEM 3     /* device or pinned host allocation failed            */
+#define GSL_ERR_CUDA 4      /* a CUDA runtime call failed                         */
+#define GSL_ERR_TIMEOUT 5   /* a device-side retry loop hit its iteration cap     */
+
+#define GSL_MODE_SYNC 0     /* Jacobi sweeps: every vertex reads the previous labels */
+#define GSL_MODE_ASYNC 1    /* in-place sweeps, as Algorithm 3 updates C             */
+
+#define GSL_STATS_SWEEPS 64
+
+typedef struct gsl_ctx gsl_ctx;
+
+/* Symmetric CSR on the device.  0 <= n < 2^31; offsets has n+1 entries with
+ * offsets[0] = 0, offsets[i] <= offsets[i+1], offsets[n] = nnz; cols has nnz
+ * entries, each in [0, n). */
+typedef struct gsl_csr {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* offsets;
+  const int32_t* cols;
+} gsl_csr;
+
+/* Per-call statistics (host struct, optional). */
+typedef struct gsl_stats {
+  int32_t iterations;                 /* sweeps performed (l_i of Algorithm 3)          */
+  int32_t converged;                  /* 1: stopped by dN/N <= tolerance; 0: max_iters  */
+  int64_t changed[GSL_STATS_SWEEPS];  /* dN of sweep t (t < 64)                          */
+  int64_t active[GSL_STATS_SWEEPS];   /* vertices processed in sweep t (pruned frontier) */
+  int64_t edges_scanned;              /* CSR entries read by all sweeps                  */
+  int64_t communities;                /* after a split: number of pieces, else 0         */
+  float ms_lpa;                       /* device time of the sweep phase                  */
+  float ms_split;                     /* device time of the split phase (gsl_gsllpa)     */
+} gsl_stats;
+
+/* Creates a context on CUDA device `device`.  *ctx receives the handle. */
+int gsl_ctx_create(gsl_ctx** ctx, int device);
+
+/* Frees the context and all scratch memory it owns.  NULL is accepted. */
+int gsl_ctx_destroy(gsl_ctx* ctx);
+
+/* Degree-class thresholds of the sweep kernels: vertices of degree
+ * 33..warp_max are handled by one warp each (shared-memory table), degree
+ * warp_max+1..blk_max by one block each (shared-memory table), and larger
+ * degrees by one block each with a global-memory table.  Defaults 128 and
+ * 4096.  Requires 32 <= warp_max <= 1024 and warp_max <= blk_max, and
+ * 16*blk_max bytes must fit the device's shared memory per block.  Results
+ * do not depend on these values. */
+int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
+
+/* Label propagation: lpa() of Algorithm 3 without its final split (the
+ * "GVE-LPA" phase).  Labels start as labels_init (device int32[n], values
+ * in [0, n)) or, when labels_init is NULL, as C = [0 .. n).  Each sweep
+ * moves every vertex i of the frontier to
+ *     argmax_c  sum_{j in J_i, j != i, C_j = c} w_ij         (Eq. 2)
+ * with ties to the smallest label, and keeps the label of a vertex with no
+ * neighbour other than itself.  The frontier is every vertex in sweep 1
+ * and afterwards the changed vertices and their neighbours (the pruning of
+ * lpaMove()).  After sweep t the call stops if dN_t / n <= tolerance or
+ * t = max_iters.
+ *   weights     device int32[nnz], every entry >= 1, or NULL for unit weights
+ *               (Section 3).  Sums are exact int32: every weighted degree
+ *               must be < 2^31 (else GSL_ERR_OVERFLOW).
+ *   tolerance   tau >= 0 of Algorithm 3.
+ *   max_iters   MAX_ITERATIONS >= 0; 0 returns the initial labels.
+ *   mode        GSL_MODE_SYNC: Jacobi sweeps, deterministic, equal to the
+ *               unpruned synchronous definition label for label.
+ *               GSL_MODE_ASYNC: labels updated in place, so a vertex may
+ *               see neighbours already moved in the same sweep; the result
+ *               depends on scheduling.
+ *   labels_out  device int32[n]; may equal labels_init.
+ *   stats       optional host struct.
+ */
+int gsl_lpa(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, const int32_t* labels_init,
+            double tolerance, int32_t max_iters, int32_t mode, int32_t* labels_out,
+            gsl_stats* stats, void* stream);
+
+/* Split last: splitDisconnectedBfs() of Algorithm 2.  labels_out[v] becomes
+ * the smallest vertex id of the connected piece of v's community that holds
+ * v, where the pieces are the connected components of the subgraph of edges
+ * (u, v) with labels_in[u] == labels_in[v].  This is the labelling Algorithm
+ * 2 produces when each BFS starts from the first unvisited vertex in
+ * ascending order (and the fixed point of Algorithm 1).
+ *   labels_in   device int32[n], any values (only compared for equality).
+ *   labels_out  device int32[n]; may equal labels_in.
+ *   renumber    0: pieces keep their smallest-vertex-id labels;
+ *               1: pieces are numbered 0..k-1 in increasing order of their
+ *                  smallest vertex id.
+ *   k_out       optional HOST pointer receiving k, the number of pieces.
+ */
+int gsl_split(gsl_ctx* ctx, const gsl_csr* g, const int32_t* labels_in, int32_t* labels_out,
+              int32_t renumber, int64_t* k_out, void* stream);
+
+/* Modularity, Eq. 1:  Q = sum_c [ sigma_c / 2m - (Sigma_c / 2m)^2 ], with
+ * 2m the sum of all entry weights, sigma_c the weight of entries inside c
+ * and Sigma_c the summed weighted degree of c's vertices.  The three sums
+ * are exact integers (Sigma_c^2 summed in 128 bits) and Q is formed once in
+ * double; an empty graph gives 0.
+ *   labels   device int32[n], values in [0, n) (else GSL_ERR_INVALID).
+ *   q_out    HOST double.
+ */
+int gsl_modularity(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, const int32_t* labels,
+                   double* q_out, void* stream);
+
+/* GSL-LPA: lpa() of Algorithm 3 including its final split, i.e. gsl_lpa
+ * from C = [0 .. n) followed by gsl_split with renumber = 0.  labels_out
+ * receives connected-community labels (smallest vertex id of each piece). */
+int gsl_gsllpa(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, double tolerance,
+               int32_t max_iters, int32_t mode, int32_t* labels_out, gsl_stats* stats,
+               void* stream);
+
+/* gsl_gsllpa on HOST buffers: copies offsets, cols and weights (nullable) to
+ * the device, runs GSL-LPA and copies the labels back to labels_out_host
+ * (host int32[n]).  Device copies of the graph are context scratch.  Host
+ * buffers may be pageable or pinned (pinned is faster). */
+int gsl_gsllpa_host(gsl_ctx* ctx, int64_t n, int64_t nnz, const int64_t* offsets_host,
+                    const int32_t* cols_host, const int32_t* weights_host, double tolerance,
+                    int32_t max_iters, int32_t mode, int32_t* labels_out_host, gsl_stats* stats,
+                    void* stream);
+
+/* Profiling.  When enabled on a context, every launch sequence of the
+ * context is bracketed by CUDA events on the call's stream and its device
+ * time, vertex and entry counts and algorithmic bytes are accumulated per
+ * slot (frontier binning, each degree class of the sweep, union-find split,
+ * piece count / renumbering, modularity, ...).  Algorithmic bytes count each
+ * array element the definition has to touch once (a CSR column, a gathered
+ * label, a written label), not the sectors the hardware moves.
+ * gsl_ctx_set_profiling(ctx, 1) enables and zeroes the accumulators; 0
+ * disables.  Enabling adds two event records per launch sequence. */
+#define GSL_PROFILE_SLOTS 24
+typedef struct gsl_profile_slot {
+  char name[32];
+  int64_t launches;   /* launch sequences timed          */
+  int64_t kernels;    /* kernels in those sequences       */
+  double ms;          /* summed CUDA-event device time    */
+  int64_t vertices;   /* vertices processed               */
+  int64_t entries;    /* CSR entries read                 */
+  double bytes;       /* algorithmic bytes                */
+} gsl_profile_slot;
+typedef struct gsl_profile {
+  int32_t nslots;
+  gsl_profile_slot slot[GSL_PROFILE_SLOTS];
+} gsl_profile;
+int gsl_ctx_set_profiling(gsl_ctx* ctx, int32_t enable);
+int gsl_ctx_get_profile(gsl_ctx* ctx, gsl_profile* out);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t gsl_kernel_launches(void);
+
+/* Static message for an error code. */
+const char* gsl_strerror(int code);
+
+/* Detail of the last error on ctx ("" if none).  Valid until the next call. */
+const char* gsl_ctx_last_error(gsl_ctx* ctx);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int gsl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSLLPA_H */

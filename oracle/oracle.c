@@ -118,7 +118,7 @@ int32_t oracle_lpa_seq(int64_t n, const int64_t* off, const int32_t* col, const 
                        const int32_t* labels_init, double tau, int32_t max_iters,
                        int32_t* C, int64_t* dn_per_sweep) {
   for (int64_t i = 0; i < n; ++i) C[i] = labels_init ? labels_init[i] : (int32_t)i;
-  if (n == 0) return 0;
+  if (n <= 0) return 0;
   int64_t* W = (int64_t*)calloc((size_t)n, sizeof(int64_t));
   int32_t* touched = (int32_t*)malloc(sizeof(int32_t) * (size_t)(max_degree(n, off) + 1));
   uint8_t* processed = (uint8_t*)calloc((size_t)n, 1);     /* all unprocessed */
@@ -265,7 +265,7 @@ int64_t oracle_disconnected(int64_t n, const int64_t* off, const int32_t* col, c
     if (C[i] < 0 || C[i] >= n) { free(S); free(vis); free(queue); return -1; }
     S[C[i]]++;
   }
-  if (D) memset(D, 0, (size_t)n);
+  if (D && n > 0) memset(D, 0, (size_t)n);
   int64_t flagged = 0;
   for (int64_t i = 0; i < n; ++i) {
     int32_t c = C[i];

@@ -1,0 +1,246 @@
+"""GB300 (sm_103a) GSL-LPA: label propagation with split-last, on one GPU.
+
+Thin Python binding over the C ABI of ``include/gsllpa.h`` (libgsllpa.so):
+argument marshalling only, every step runs in the library's CUDA kernels.
+There is no CPU fallback; if the library cannot be loaded the import of a
+function fails with an error.  PyTorch supplies device memory and streams.
+
+    import paper_2403_01261_gb300 as gsl
+    labels = gsl.gsllpa(offsets, cols)            # torch CUDA tensors
+    q = gsl.modularity(offsets, cols, labels)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+__all__ = ["Stats", "Context", "GslError", "lpa", "split", "modularity", "gsllpa", "gsllpa_host", "library_path",
+           "load", "MODE_SYNC", "MODE_ASYNC"]
+
+MODE_SYNC = 0
+MODE_ASYNC = 1
+STATS_SWEEPS = 64
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GslError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gsl error {code}: {msg}")
+        self.code = code
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("cols", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("changed", ctypes.c_int64 * STATS_SWEEPS), ("active", ctypes.c_int64 * STATS_SWEEPS),
+                ("edges_scanned", ctypes.c_int64), ("communities", ctypes.c_int64),
+                ("ms_lpa", ctypes.c_float), ("ms_split", ctypes.c_float)]
+
+    def as_dict(self):
+        t = min(self.iterations, STATS_SWEEPS)
+        return {"iterations": self.iterations, "converged": bool(self.converged),
+                "changed": list(self.changed[:t]), "active": list(self.active[:t]),
+                "edges_scanned": self.edges_scanned, "communities": self.communities,
+                "ms_lpa": self.ms_lpa, "ms_split": self.ms_split}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libgsllpa.so, building it with nvcc first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sp = ctypes.POINTER(Stats)
+        cp = ctypes.POINTER(Csr)
+        lib.gsl_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
+        lib.gsl_ctx_destroy.argtypes = [P]
+        lib.gsl_ctx_set_tuning.argtypes = [P, i32, i32]
+        lib.gsl_lpa.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
+        lib.gsl_split.argtypes = [P, cp, P, P, i32, ctypes.POINTER(i64), P]
+        lib.gsl_modularity.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
+        lib.gsl_gsllpa.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
+        lib.gsl_gsllpa_host.argtypes = [P, i64, i64, P, P, P, dbl, i32, i32, P, sp, P]
+        lib.gsl_strerror.restype = ctypes.c_char_p
+        lib.gsl_strerror.argtypes = [ctypes.c_int]
+        lib.gsl_ctx_last_error.restype = ctypes.c_char_p
+        lib.gsl_ctx_last_error.argtypes = [P]
+        lib.gsl_version.restype = ctypes.c_int
+        for name in ("gsl_ctx_create", "gsl_ctx_destroy", "gsl_ctx_set_tuning", "gsl_lpa", "gsl_split",
+                     "gsl_modularity", "gsl_gsllpa", "gsl_gsllpa_host"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_graph(offsets, cols, weights=None):
+    import torch
+    if not (offsets.is_cuda and cols.is_cuda):
+        raise ValueError("offsets and cols must be CUDA tensors")
+    if offsets.dtype != torch.int64 or cols.dtype != torch.int32:
+        raise TypeError("offsets must be int64 and cols int32")
+    if not (offsets.is_contiguous() and cols.is_contiguous()):
+        raise ValueError("offsets and cols must be contiguous")
+    if weights is not None and (weights.dtype != torch.int32 or not weights.is_cuda or not weights.is_contiguous()
+                                or weights.numel() != cols.numel()):
+        raise TypeError("weights must be a contiguous int32 CUDA tensor with one entry per column")
+    c = Csr()
+    c.n = offsets.numel() - 1
+    c.nnz = cols.numel()
+    c.offsets = offsets.data_ptr()
+    c.cols = cols.data_ptr() if cols.numel() else None
+    return c
+
+
+class Context:
+    """One library context (scratch memory) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        self.device = device
+        rc = self._lib.gsl_ctx_create(ctypes.byref(self._h), device)
+        if rc != 0:
+            raise GslError(rc, self._lib.gsl_strerror(rc).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.gsl_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 -- interpreter shutdown
+            pass
+
+    def _raise(self, rc):
+        if rc != 0:
+            raise GslError(rc, f"{self._lib.gsl_strerror(rc).decode()}: {self._lib.gsl_ctx_last_error(self._h).decode()}")
+
+    def set_tuning(self, warp_max: int, blk_max: int):
+        self._raise(self._lib.gsl_ctx_set_tuning(self._h, warp_max, blk_max))
+
+    def lpa(self, offsets, cols, weights=None, labels_init=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC,
+            out=None, stream=None, stats=False):
+        import torch
+        g = _check_graph(offsets, cols, weights)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        st = Stats()
+        rc = self._lib.gsl_lpa(self._h, ctypes.byref(g), _ptr(weights), _ptr(labels_init), float(tolerance),
+                               int(max_iters), int(mode), _ptr(out), ctypes.byref(st), _stream(stream))
+        self._raise(rc)
+        return (out, st.as_dict()) if stats else out
+
+    def split(self, offsets, cols, labels, renumber=False, out=None, stream=None):
+        import torch
+        g = _check_graph(offsets, cols)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        k = ctypes.c_int64()
+        rc = self._lib.gsl_split(self._h, ctypes.byref(g), _ptr(labels), _ptr(out), int(bool(renumber)),
+                                 ctypes.byref(k), _stream(stream))
+        self._raise(rc)
+        return out, int(k.value)
+
+    def modularity(self, offsets, cols, labels, weights=None, stream=None):
+        g = _check_graph(offsets, cols, weights)
+        q = ctypes.c_double()
+        rc = self._lib.gsl_modularity(self._h, ctypes.byref(g), _ptr(weights), _ptr(labels), ctypes.byref(q),
+                                      _stream(stream))
+        self._raise(rc)
+        return q.value
+
+    def gsllpa(self, offsets, cols, weights=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC, out=None,
+               stream=None, stats=False):
+        import torch
+        g = _check_graph(offsets, cols, weights)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        st = Stats()
+        rc = self._lib.gsl_gsllpa(self._h, ctypes.byref(g), _ptr(weights), float(tolerance), int(max_iters),
+                                  int(mode), _ptr(out), ctypes.byref(st), _stream(stream))
+        self._raise(rc)
+        return (out, st.as_dict()) if stats else out
+
+    def gsllpa_host(self, offsets, cols, weights=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC, out=None,
+                    stream=None, stats=False):
+        """GSL-LPA on host tensors/arrays (CPU torch tensors, pinned preferred);
+        the copies to and from the device happen inside the call."""
+        import torch
+        offsets = torch.as_tensor(offsets)
+        cols = torch.as_tensor(cols)
+        if offsets.dtype != torch.int64 or cols.dtype != torch.int32 or offsets.is_cuda or cols.is_cuda:
+            raise TypeError("host offsets int64 and cols int32 expected")
+        n = offsets.numel() - 1
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32)
+        if weights is not None:
+            weights = torch.as_tensor(weights)
+        st = Stats()
+        rc = self._lib.gsl_gsllpa_host(self._h, n, cols.numel(), _ptr(offsets), _ptr(cols), _ptr(weights),
+                                       float(tolerance), int(max_iters), int(mode), _ptr(out), ctypes.byref(st),
+                                       _stream(stream))
+        self._raise(rc)
+        return (out, st.as_dict()) if stats else out
+
+
+_default = {}
+
+
+def _ctx(device=None) -> Context:
+    import torch
+    d = torch.cuda.current_device() if device is None else int(device)
+    with _lock:
+        if d not in _default:
+            _default[d] = None
+    if _default[d] is None:
+        _default[d] = Context(d)
+    return _default[d]
+
+
+def lpa(offsets, cols, weights=None, **kw):
+    return _ctx(offsets.device.index).lpa(offsets, cols, weights, **kw)
+
+
+def split(offsets, cols, labels, **kw):
+    return _ctx(offsets.device.index).split(offsets, cols, labels, **kw)
+
+
+def modularity(offsets, cols, labels, weights=None, **kw):
+    return _ctx(offsets.device.index).modularity(offsets, cols, labels, weights, **kw)
+
+
+def gsllpa(offsets, cols, weights=None, **kw):
+    return _ctx(offsets.device.index).gsllpa(offsets, cols, weights, **kw)
+
+
+def gsllpa_host(offsets, cols, weights=None, device=0, **kw):
+    return _ctx(device).gsllpa_host(offsets, cols, weights, **kw)

@@ -1,0 +1,658 @@
+// gsllpa.cu -- host orchestration and C ABI of the GSL-LPA library.
+//
+// lpa() of Algorithm 3 runs as a host loop of sweeps: bin the frontier by
+// degree class, launch the class kernels, read the change count back, stop
+// when dN/N <= tolerance or after max_iters sweeps.  The split of Algorithm
+// 2 and the modularity of Eq. 1 follow as separate kernel sequences.  The
+// context owns all scratch memory and grows it on demand.
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gsllpa.h"
+#include "kernels.h"
+
+using namespace gsl;
+
+struct gsl_ctx {
+  int device = 0;
+  DeviceInfo di;
+  Tuning tune;
+  std::string last_error;
+
+  long long cap_n = 0;             // vertex capacity of the per-vertex scratch
+  int* lab[2] = {nullptr, nullptr};
+  unsigned char* flag[2] = {nullptr, nullptr};
+  int* work = nullptr;
+  int* parent = nullptr;
+  int* rank = nullptr;
+  unsigned long long* sigma = nullptr;
+  long long cap_sigma = 0;
+  unsigned long long* block_sums = nullptr;
+  long long cap_blocks = 0;
+  unsigned long long* partials = nullptr;
+  long long cap_partials = 0;
+
+  unsigned* hub_keys = nullptr;
+  unsigned* hub_vals = nullptr;
+  long long cap_hub = 0;           // slots per array
+
+  Counters* ctr = nullptr;         // device
+  Counters* ctr_h = nullptr;       // pinned host mirror
+  ModSums* sums = nullptr;         // device
+  ModSums* sums_h = nullptr;       // pinned
+  unsigned long long* k_dev = nullptr;
+  unsigned long long* k_h = nullptr;
+
+  // staging of the host-buffer entry point
+  long long* st_off = nullptr;
+  long long cap_st_off = 0;
+  int* st_col = nullptr;
+  long long cap_st_col = 0;
+  int* st_w = nullptr;
+  long long cap_st_w = 0;
+  int* st_lab = nullptr;
+  long long cap_st_lab = 0;
+
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+  // profiling (gsl_ctx_set_profiling): CUDA-event time per launch sequence
+  bool prof = false;
+  gsl_profile profile{};
+  std::vector<cudaEvent_t> evpool;
+  struct Pending {
+    int slot, e0, e1;
+  };
+  std::vector<Pending> pending;
+  int ev_used = 0;
+};
+
+namespace {
+
+// int64_t is `long` on LP64 Linux; the kernels take `long long`.
+inline const long long* OFF(const gsl_csr* g) { return reinterpret_cast<const long long*>(g->offsets); }
+
+int fail(gsl_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->last_error = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) {                                                                         \
+      cudaGetLastError();                                                                            \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? GSL_ERR_NOMEM : GSL_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                                \
+    }                                                                                                \
+  } while (0)
+
+template <typename T>
+int grow(gsl_ctx* c, T*& ptr, long long& cap, long long need) {
+  if (need <= cap && ptr) return GSL_OK;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+  long long alloc = need > 0 ? need : 1;
+  cudaError_t e = cudaMalloc(&ptr, sizeof(T) * (size_t)alloc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    return fail(c, GSL_ERR_NOMEM, "cudaMalloc of %lld bytes failed: %s", (long long)(sizeof(T) * alloc),
+                cudaGetErrorString(e));
+  }
+  cap = alloc;
+  return GSL_OK;
+}
+
+int ensure_vertex_scratch(gsl_ctx* c, long long n) {
+  if (n <= c->cap_n && c->lab[0]) return GSL_OK;
+  long long dummy;
+  for (int i = 0; i < 2; ++i) {
+    dummy = 0;
+    if (c->lab[i]) cudaFree(c->lab[i]);
+    c->lab[i] = nullptr;
+    if (int r = grow(c, c->lab[i], dummy, n)) return r;
+    dummy = 0;
+    if (c->flag[i]) cudaFree(c->flag[i]);
+    c->flag[i] = nullptr;
+    if (int r = grow(c, c->flag[i], dummy, n)) return r;
+  }
+  dummy = 0;
+  if (c->work) cudaFree(c->work);
+  c->work = nullptr;
+  if (int r = grow(c, c->work, dummy, n)) return r;
+  dummy = 0;
+  if (c->parent) cudaFree(c->parent);
+  c->parent = nullptr;
+  if (int r = grow(c, c->parent, dummy, n)) return r;
+  dummy = 0;
+  if (c->rank) cudaFree(c->rank);
+  c->rank = nullptr;
+  if (int r = grow(c, c->rank, dummy, n)) return r;
+  c->cap_n = n;
+  return GSL_OK;
+}
+
+int check_csr(gsl_ctx* c, const gsl_csr* g) {
+  if (!g) return fail(c, GSL_ERR_INVALID, "graph is NULL");
+  if (g->n < 0 || g->n >= (1ll << 31)) return fail(c, GSL_ERR_INVALID, "n = %lld outside [0, 2^31)", (long long)g->n);
+  if (g->nnz < 0) return fail(c, GSL_ERR_INVALID, "nnz = %lld < 0", (long long)g->nnz);
+  if (!g->offsets) return fail(c, GSL_ERR_INVALID, "offsets is NULL");
+  if (g->nnz > 0 && !g->cols) return fail(c, GSL_ERR_INVALID, "cols is NULL");
+  return GSL_OK;
+}
+
+int map_err(gsl_ctx* c, int bits, const char* where) {
+  if (bits & ERRBIT_INVALID) return fail(c, GSL_ERR_INVALID, "%s: malformed graph or labels (offsets, column, weight or label out of range)", where);
+  if (bits & ERRBIT_OVERFLOW) return fail(c, GSL_ERR_OVERFLOW, "%s: a weighted degree is >= 2^31", where);
+  if (bits & ERRBIT_TIMEOUT) return fail(c, GSL_ERR_TIMEOUT, "%s: a device retry loop hit its bound", where);
+  return GSL_OK;
+}
+
+// ------------------------------------------------------------- profiling
+enum Slot { SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + NCLASS, SL_COUNT, SL_MOD, SL_N };
+const char* slot_name(int k) {
+  static const char* names[SL_N] = {"classify", "init_labels", "bin_frontier", "sweep_deg1", "sweep_deg2",
+                                    "sweep_deg3_4", "sweep_deg5_8", "sweep_deg9_16", "sweep_deg17_32",
+                                    "sweep_warp", "sweep_block", "sweep_hub", "split_unionfind",
+                                    "split_count_renumber", "modularity"};
+  return names[k];
+}
+
+int prof_begin(gsl_ctx* c, cudaStream_t s) {
+  if (!c->prof) return -1;
+  while ((int)c->evpool.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    c->evpool.push_back(e);
+  }
+  const int e0 = c->ev_used;
+  c->ev_used += 2;
+  cudaEventRecord(c->evpool[e0], s);
+  return e0;
+}
+
+void prof_end(gsl_ctx* c, int e0, int slot, cudaStream_t s, long long kernels) {
+  if (e0 < 0) return;
+  cudaEventRecord(c->evpool[e0 + 1], s);
+  c->pending.push_back({slot, e0, e0 + 1});
+  c->profile.slot[slot].launches += 1;
+  c->profile.slot[slot].kernels += kernels;
+}
+
+// Call after the stream has been synchronised.
+void prof_resolve(gsl_ctx* c) {
+  for (const auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->evpool[p.e0], c->evpool[p.e1]) == cudaSuccess) c->profile.slot[p.slot].ms += ms;
+    else cudaGetLastError();
+  }
+  c->pending.clear();
+  c->ev_used = 0;
+}
+
+// Resets all counters, classifies every vertex by degree (validating the
+// offsets) and sizes the hub tables.  Synchronises the stream.
+int prepare_graph(gsl_ctx* c, const gsl_csr* g, cudaStream_t s) {
+  CK(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+  const int pe = prof_begin(c, s);
+  CK(launch_class_histogram(OFF(g), g->n, g->nnz, c->tune, c->ctr, c->di, s));
+  prof_end(c, pe, SL_CLASSIFY, s, 2);
+  c->profile.slot[SL_CLASSIFY].vertices += g->n;
+  c->profile.slot[SL_CLASSIFY].bytes += 8.0 * (double)(g->n + 1);
+  CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  prof_resolve(c);
+  if (int r = map_err(c, c->ctr_h->err, "offsets")) return r;
+  if (c->ctr_h->max_degree > c->tune.blk_max) {
+    const long long region = 2 * c->ctr_h->max_degree;
+    const long long need = region * hub_grid_size(c->tune, c->di);
+    long long ck = c->cap_hub, cv = c->cap_hub;
+    if (int r = grow(c, c->hub_keys, ck, need)) return r;
+    if (int r = grow(c, c->hub_vals, cv, need)) return r;
+    c->cap_hub = need;
+  }
+  return GSL_OK;
+}
+
+long long hub_region(gsl_ctx* c) { return 2 * c->ctr_h->max_degree; }
+
+int reset_sweep_counters(gsl_ctx* c, cudaStream_t s) {
+  CK(cudaMemsetAsync(c->ctr, 0, offsetof(Counters, err), s));
+  return GSL_OK;
+}
+
+// The sweep loop.  On success *final points at the scratch buffer holding
+// the labels.  prepare_graph must have run.
+int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t* labels_init, double tol,
+            int32_t max_iters, int32_t mode, gsl_stats* st, cudaStream_t s, int** final) {
+  const long long n = g->n;
+  const bool async_mode = mode == GSL_MODE_ASYNC;
+  CK(cudaMemsetAsync(c->flag[0], 0, (size_t)n, s));
+  CK(cudaMemsetAsync(c->flag[1], 0, (size_t)n, s));
+  {
+    const int pe = prof_begin(c, s);
+    CK(launch_init_labels(labels_init, c->lab[0], async_mode ? nullptr : c->lab[1], n, c->ctr, c->di, s));
+    prof_end(c, pe, SL_INIT, s, 1);
+    c->profile.slot[SL_INIT].vertices += n;
+    c->profile.slot[SL_INIT].bytes += (double)n * ((labels_init ? 4.0 : 0.0) + (async_mode ? 4.0 : 8.0));
+  }
+  SweepArgs a{};
+  a.off = OFF(g);
+  a.col = g->cols;
+  a.w = weights;
+  a.ctr = c->ctr;
+  a.work = c->work;
+  a.hub_keys = c->hub_keys;
+  a.hub_vals = c->hub_vals;
+  a.hub_region = hub_region(c);
+  a.n = n;
+  int t = 0;
+  bool converged = false, marked_prev = false;
+  long long dn_prev = n;
+  long long scanned = 0;
+  while (t < max_iters) {
+    ++t;
+    if (int r = reset_sweep_counters(c, s)) return r;
+    const bool all_active = t == 1 || !marked_prev;
+    {
+      const int pe = prof_begin(c, s);
+      CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s));
+      prof_end(c, pe, SL_BIN, s, 1);
+    }
+    if (async_mode) {
+      a.prev = c->lab[0];
+      a.next = c->lab[0];
+    } else {
+      a.prev = c->lab[(t - 1) & 1];
+      a.next = c->lab[t & 1];
+    }
+    a.fnext = c->flag[(t + 1) & 1];
+    a.ident = (!async_mode && !labels_init && t == 1) ? 1 : 0;
+    a.check = t == 1 ? 1 : 0;
+    // Sweep 1 changes every vertex that has a neighbour, and a sweep after
+    // one that changed more than half of the vertices is run on all
+    // vertices: marking would select nearly everything anyway.
+    a.mark = (t > 1 && 2 * dn_prev <= n) ? 1 : 0;
+    for (int k = 0; k < NCLASS; ++k) {
+      const int pe = prof_begin(c, s);
+      CK(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, s));
+      prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+    }
+    CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->prof) {
+      prof_resolve(c);
+      // algorithmic bytes: per processed vertex its two offsets (8 B, shared
+      // with the next row), worklist entry, own label (not read from the
+      // identity labelling) and label write; per entry the column, the
+      // neighbour's label (not read from the identity labelling) and weight
+      const double per_v = 8.0 + 4.0 + (a.ident ? 0.0 : 4.0) + 4.0;
+      const double per_e = 4.0 + (a.ident ? 0.0 : 4.0) + (weights ? 4.0 : 0.0);
+      long long act_all = 0;
+      for (int k = 0; k < NCLASS; ++k) {
+        auto& sl = c->profile.slot[SL_SWEEP0 + k];
+        const long long v = c->ctr_h->cls_count[k];
+        const long long e = (long long)c->ctr_h->cls_scanned[k];
+        sl.vertices += v;
+        sl.entries += e;
+        sl.bytes += per_v * (double)v + per_e * (double)e;
+        act_all += v;
+      }
+      auto& sb = c->profile.slot[SL_BIN];
+      sb.vertices += all_active ? n : act_all;
+      sb.bytes += (all_active ? 0.0 : (double)n) + (all_active ? 16.0 * (double)n : 16.0 * (double)act_all) +
+                  4.0 * (double)act_all;
+    }
+    if (int r = map_err(c, c->ctr_h->err, "lpa")) return r;
+    const long long dn = (long long)c->ctr_h->dn;
+    long long act = 0;
+    for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
+    scanned += (long long)c->ctr_h->scanned;
+    if (st && t <= GSL_STATS_SWEEPS) {
+      st->changed[t - 1] = dn;
+      st->active[t - 1] = act;
+    }
+    marked_prev = a.mark != 0;
+    dn_prev = dn;
+    if ((double)dn / (double)n <= tol) {
+      converged = true;
+      break;
+    }
+  }
+  if (st) {
+    st->iterations = t;
+    st->converged = converged ? 1 : 0;
+    st->edges_scanned = scanned;
+  }
+  *final = async_mode ? c->lab[0] : c->lab[t & 1];
+  return GSL_OK;
+}
+
+int run_split(gsl_ctx* c, const gsl_csr* g, const int32_t* labels_in, int32_t* labels_out, int32_t renumber,
+              long long* k, cudaStream_t s) {
+  const long long n = g->n;
+  if (int r = reset_sweep_counters(c, s)) return r;
+  int pe = prof_begin(c, s);
+  CK(launch_bin(OFF(g), n, nullptr, 1, c->tune, c->work, c->ctr, c->di, s));
+  prof_end(c, pe, SL_BIN, s, 1);
+  c->profile.slot[SL_BIN].vertices += n;
+  c->profile.slot[SL_BIN].bytes += 20.0 * (double)n;
+  pe = prof_begin(c, s);
+  CK(launch_split(OFF(g), g->cols, n, labels_in, c->work, c->ctr, c->parent, labels_out, c->tune, c->di, s));
+  prof_end(c, pe, SL_SPLIT, s, 11);
+  // per vertex: parent init, own label, offsets, compress read and label
+  // write; per entry: the column and, for the half with j < u, the label
+  c->profile.slot[SL_SPLIT].vertices += n;
+  c->profile.slot[SL_SPLIT].entries += g->nnz;
+  c->profile.slot[SL_SPLIT].bytes += (4.0 + 4.0 + 8.0 + 4.0 + 4.0) * (double)n + 6.0 * (double)g->nnz;
+  const long long nb = renumber_blocks(n);
+  if (int r = grow(c, c->block_sums, c->cap_blocks, nb > 0 ? nb : 1)) return r;
+  pe = prof_begin(c, s);
+  if (renumber) {
+    CK(launch_renumber(labels_out, labels_out, n, c->rank, c->block_sums, c->cap_blocks, c->k_dev, c->di, s));
+  } else {
+    // count the pieces (representatives) without renumbering
+    CK(launch_renumber(labels_out, nullptr, n, c->rank, c->block_sums, c->cap_blocks, c->k_dev, c->di, s));
+  }
+  prof_end(c, pe, SL_COUNT, s, renumber ? 4 : 2);
+  c->profile.slot[SL_COUNT].vertices += n;
+  c->profile.slot[SL_COUNT].bytes += (renumber ? 4.0 * 4.0 : 4.0) * (double)n;
+  CK(cudaMemcpyAsync(c->k_h, c->k_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  prof_resolve(c);
+  if (int r = map_err(c, c->ctr_h->err, "split")) return r;
+  *k = (long long)*c->k_h;
+  return GSL_OK;
+}
+
+int run_modularity(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t* labels, double* q,
+                   cudaStream_t s) {
+  const long long n = g->n;
+  if (int r = grow(c, c->sigma, c->cap_sigma, n)) return r;
+  const long long np = modularity_partials(c->di);
+  if (int r = grow(c, c->partials, c->cap_partials, 2 * np)) return r;
+  CK(cudaMemsetAsync(c->sigma, 0, sizeof(unsigned long long) * (size_t)n, s));
+  CK(cudaMemsetAsync(c->sums, 0, sizeof(ModSums), s));
+  if (int r = reset_sweep_counters(c, s)) return r;
+  CK(launch_bin(OFF(g), n, nullptr, 1, c->tune, c->work, c->ctr, c->di, s));
+  const int pe = prof_begin(c, s);
+  CK(launch_modularity(OFF(g), g->cols, weights, n, labels, c->work, c->ctr, c->sigma, c->partials, np, c->sums,
+                       c->tune, c->di, s));
+  prof_end(c, pe, SL_MOD, s, 12);
+  // per vertex: offsets, label, Sigma update (read+write) and square pass;
+  // per entry: column, neighbour label and weight
+  c->profile.slot[SL_MOD].vertices += n;
+  c->profile.slot[SL_MOD].entries += g->nnz;
+  c->profile.slot[SL_MOD].bytes += (8.0 + 4.0 + 16.0 + 8.0) * (double)n + (8.0 + (weights ? 4.0 : 0.0)) * (double)g->nnz;
+  CK(cudaMemcpyAsync(c->sums_h, c->sums, sizeof(ModSums), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  prof_resolve(c);
+  if (int r = map_err(c, c->ctr_h->err, "modularity")) return r;
+  const ModSums& m = *c->sums_h;
+  if (m.two_m == 0) {
+    *q = 0.0;
+    return GSL_OK;
+  }
+  const unsigned __int128 s2 = ((unsigned __int128)m.s2_hi << 64) | m.s2_lo;
+  const double dm = (double)m.two_m;
+  *q = (double)m.s1 / dm - (double)s2 / (dm * dm);
+  return GSL_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int check_lpa_args(gsl_ctx* c, const gsl_csr* g, double tol, int32_t max_iters, int32_t mode, const void* out) {
+  if (int r = check_csr(c, g)) return r;
+  if (!(tol >= 0.0)) return fail(c, GSL_ERR_INVALID, "tolerance must be >= 0");
+  if (max_iters < 0) return fail(c, GSL_ERR_INVALID, "max_iters must be >= 0");
+  if (mode != GSL_MODE_SYNC && mode != GSL_MODE_ASYNC) return fail(c, GSL_ERR_INVALID, "unknown mode %d", mode);
+  if (g->n > 0 && !out) return fail(c, GSL_ERR_INVALID, "labels_out is NULL");
+  return GSL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsl_version(void) { return 100; }
+
+const char* gsl_strerror(int code) {
+  switch (code) {
+    case GSL_OK: return "ok";
+    case GSL_ERR_INVALID: return "invalid argument or malformed input";
+    case GSL_ERR_OVERFLOW: return "weighted degree overflows int32";
+    case GSL_ERR_NOMEM: return "out of memory";
+    case GSL_ERR_CUDA: return "CUDA error";
+    case GSL_ERR_TIMEOUT: return "device retry bound reached";
+    default: return "unknown error";
+  }
+}
+
+const char* gsl_ctx_last_error(gsl_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+int gsl_ctx_create(gsl_ctx** out, int device) {
+  if (!out) return GSL_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GSL_ERR_CUDA;
+  }
+  gsl_ctx* c = new gsl_ctx();
+  c->device = device;
+  DeviceGuard dg(device);
+  cudaDeviceGetAttribute(&c->di.sm_count, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&c->di.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  bool ok = cudaMalloc(&c->ctr, sizeof(Counters)) == cudaSuccess &&
+            cudaMallocHost(&c->ctr_h, sizeof(Counters)) == cudaSuccess &&
+            cudaMalloc(&c->sums, sizeof(ModSums)) == cudaSuccess &&
+            cudaMallocHost(&c->sums_h, sizeof(ModSums)) == cudaSuccess &&
+            cudaMalloc(&c->k_dev, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMallocHost(&c->k_h, sizeof(unsigned long long)) == cudaSuccess;
+  for (int i = 0; ok && i < 4; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gsl_ctx_destroy(c);
+    return GSL_ERR_NOMEM;
+  }
+  memset(c->ctr_h, 0, sizeof(Counters));
+  *out = c;
+  return GSL_OK;
+}
+
+int gsl_ctx_destroy(gsl_ctx* c) {
+  if (!c) return GSL_OK;
+  DeviceGuard dg(c->device);
+  void* dptrs[] = {c->lab[0], c->lab[1], c->flag[0], c->flag[1], c->work, c->parent, c->rank, c->sigma,
+                   c->block_sums, c->partials, c->hub_keys, c->hub_vals, c->ctr, c->sums, c->k_dev,
+                   c->st_off, c->st_col, c->st_w, c->st_lab};
+  for (void* p : dptrs)
+    if (p) cudaFree(p);
+  if (c->ctr_h) cudaFreeHost(c->ctr_h);
+  if (c->sums_h) cudaFreeHost(c->sums_h);
+  if (c->k_h) cudaFreeHost(c->k_h);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->evpool) cudaEventDestroy(e);
+  delete c;
+  return GSL_OK;
+}
+
+int gsl_ctx_set_tuning(gsl_ctx* c, int32_t warp_max, int32_t blk_max) {
+  if (!c) return GSL_ERR_INVALID;
+  if (warp_max < 32 || warp_max > 1024 || blk_max < warp_max)
+    return fail(c, GSL_ERR_INVALID, "need 32 <= warp_max <= 1024 and blk_max >= warp_max");
+  const long long smem_blk = 2ll * 2 * blk_max * (long long)sizeof(unsigned) + 1024;
+  if (smem_blk > c->di.max_smem_optin)
+    return fail(c, GSL_ERR_INVALID, "blk_max %d needs %lld bytes of shared memory (max %d)", blk_max, smem_blk,
+                c->di.max_smem_optin);
+  c->tune.warp_max = warp_max;
+  c->tune.blk_max = blk_max;
+  return GSL_OK;
+}
+
+int gsl_ctx_set_profiling(gsl_ctx* c, int32_t enable) {
+  if (!c) return GSL_ERR_INVALID;
+  c->prof = enable != 0;
+  memset(&c->profile, 0, sizeof(c->profile));
+  c->pending.clear();
+  c->ev_used = 0;
+  return GSL_OK;
+}
+
+int gsl_ctx_get_profile(gsl_ctx* c, gsl_profile* out) {
+  if (!c || !out) return GSL_ERR_INVALID;
+  *out = c->profile;
+  out->nslots = SL_N;
+  for (int k = 0; k < SL_N; ++k) {
+    strncpy(out->slot[k].name, slot_name(k), sizeof(out->slot[k].name) - 1);
+    out->slot[k].name[sizeof(out->slot[k].name) - 1] = 0;
+  }
+  return GSL_OK;
+}
+
+int64_t gsl_kernel_launches(void) { return launches_total(); }
+
+int gsl_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t* labels_init, double tol,
+            int32_t max_iters, int32_t mode, int32_t* labels_out, gsl_stats* st, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_lpa_args(c, g, tol, max_iters, mode, labels_out)) return r;
+  if (st) memset(st, 0, sizeof(*st));
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  CK(cudaEventRecord(c->ev[0], s));
+  if (int r = prepare_graph(c, g, s)) return r;
+  int* fin = nullptr;
+  if (int r = run_lpa(c, g, weights, labels_init, tol, max_iters, mode, st, s, &fin)) return r;
+  CK(cudaMemcpyAsync(labels_out, fin, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaEventRecord(c->ev[1], s));
+  CK(cudaEventSynchronize(c->ev[1]));
+  if (st) cudaEventElapsedTime(&st->ms_lpa, c->ev[0], c->ev[1]);
+  return GSL_OK;
+}
+
+int gsl_split(gsl_ctx* c, const gsl_csr* g, const int32_t* labels_in, int32_t* labels_out, int32_t renumber,
+              int64_t* k_out, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_csr(c, g)) return r;
+  if (g->n > 0 && (!labels_in || !labels_out)) return fail(c, GSL_ERR_INVALID, "labels pointer is NULL");
+  if (renumber != 0 && renumber != 1) return fail(c, GSL_ERR_INVALID, "renumber must be 0 or 1");
+  if (g->n == 0) {
+    if (k_out) *k_out = 0;
+    return GSL_OK;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  if (int r = prepare_graph(c, g, s)) return r;
+  long long k = 0;
+  if (int r = run_split(c, g, labels_in, labels_out, renumber, &k, s)) return r;
+  if (k_out) *k_out = k;
+  return GSL_OK;
+}
+
+int gsl_modularity(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t* labels, double* q_out,
+                   void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_csr(c, g)) return r;
+  if (!q_out) return fail(c, GSL_ERR_INVALID, "q_out is NULL");
+  if (g->n > 0 && !labels) return fail(c, GSL_ERR_INVALID, "labels is NULL");
+  *q_out = 0.0;
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  if (int r = prepare_graph(c, g, s)) return r;
+  return run_modularity(c, g, weights, labels, q_out, s);
+}
+
+int gsl_gsllpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, double tol, int32_t max_iters, int32_t mode,
+               int32_t* labels_out, gsl_stats* st, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_lpa_args(c, g, tol, max_iters, mode, labels_out)) return r;
+  if (st) memset(st, 0, sizeof(*st));
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  CK(cudaEventRecord(c->ev[0], s));
+  if (int r = prepare_graph(c, g, s)) return r;
+  int* fin = nullptr;
+  if (int r = run_lpa(c, g, weights, nullptr, tol, max_iters, mode, st, s, &fin)) return r;
+  CK(cudaEventRecord(c->ev[1], s));
+  long long k = 0;
+  if (int r = run_split(c, g, fin, labels_out, 0, &k, s)) return r;
+  CK(cudaEventRecord(c->ev[2], s));
+  CK(cudaEventSynchronize(c->ev[2]));
+  if (st) {
+    cudaEventElapsedTime(&st->ms_lpa, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&st->ms_split, c->ev[1], c->ev[2]);
+    st->communities = k;
+  }
+  return GSL_OK;
+}
+
+int gsl_gsllpa_host(gsl_ctx* c, int64_t n, int64_t nnz, const int64_t* offsets_host, const int32_t* cols_host,
+                    const int32_t* weights_host, double tol, int32_t max_iters, int32_t mode,
+                    int32_t* labels_out_host, gsl_stats* st, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 0 || n >= (1ll << 31) || nnz < 0) return fail(c, GSL_ERR_INVALID, "bad sizes n=%lld nnz=%lld", (long long)n, (long long)nnz);
+  if (!offsets_host || (nnz > 0 && !cols_host) || (n > 0 && !labels_out_host))
+    return fail(c, GSL_ERR_INVALID, "host pointer is NULL");
+  if (st) memset(st, 0, sizeof(*st));
+  if (n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = grow(c, c->st_off, c->cap_st_off, n + 1)) return r;
+  if (int r = grow(c, c->st_col, c->cap_st_col, nnz)) return r;
+  if (weights_host)
+    if (int r = grow(c, c->st_w, c->cap_st_w, nnz)) return r;
+  if (int r = grow(c, c->st_lab, c->cap_st_lab, n)) return r;
+  CK(cudaMemcpyAsync(c->st_off, offsets_host, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
+  if (nnz > 0) CK(cudaMemcpyAsync(c->st_col, cols_host, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+  if (weights_host && nnz > 0)
+    CK(cudaMemcpyAsync(c->st_w, weights_host, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+  gsl_csr g{n, nnz, reinterpret_cast<const int64_t*>(c->st_off), c->st_col};
+  if (int r = gsl_gsllpa(c, &g, weights_host ? c->st_w : nullptr, tol, max_iters, mode, c->st_lab, st, stream))
+    return r;
+  CK(cudaMemcpyAsync(labels_out_host, c->st_lab, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return GSL_OK;
+}
+
+}  // extern "C"

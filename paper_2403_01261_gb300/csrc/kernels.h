@@ -1,0 +1,79 @@
+// kernels.h -- host-side launchers of the GSL-LPA kernels (internal header).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace gsl {
+
+// Arguments of one label-propagation sweep.
+struct SweepArgs {
+  const long long* off;      // CSR offsets [n+1]
+  const int* col;            // CSR columns [nnz]
+  const int* w;              // weights [nnz] or nullptr (unit)
+  const int* prev;           // labels read (C^{t-1}); == next in async mode
+  int* next;                 // labels written (C^t)
+  unsigned char* fnext;      // frontier flags of the next sweep (set, never cleared here)
+  const int* work;           // worklist (class regions at Counters::cls_start)
+  Counters* ctr;
+  unsigned* hub_keys;        // global hash tables of the hub kernel, one region per block
+  unsigned* hub_vals;
+  long long hub_region;      // slots per block region
+  long long n;
+  int ident;                 // prev is the identity labelling (not read)
+  int check;                 // validate weights and weighted degrees
+  int mark;                  // mark neighbours of changed vertices in fnext
+};
+
+struct Tuning {
+  int warp_max = 128;        // class 6 upper degree bound (one warp, smem table)
+  int blk_max = 4096;        // class 7 upper degree bound (one block, smem table)
+  int group_block = 256;     // threads per block of the lane-group kernels
+  int warp_block = 256;      // threads per block of the warp kernel
+  int blk_block = 512;       // threads per block of the block kernel
+  int hub_block = 1024;      // threads per block of the hub kernel
+  int hub_grid = 0;          // blocks of the hub kernel (0: one per SM)
+};
+
+struct DeviceInfo {
+  int sm_count = 0;
+  int max_smem_optin = 0;
+};
+
+// lpa_kernels.cu
+cudaError_t launch_class_histogram(const long long* off, long long n, long long nnz, const Tuning& t,
+                                   Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, int all_active,
+                       const Tuning& t, int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_sweep(const SweepArgs& a, bool weighted, bool async_mode, const Tuning& t,
+                         const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool async_mode, const Tuning& t,
+                               const DeviceInfo& di, cudaStream_t s);
+void count_launches(long long k);   // process-wide tally of kernels this library launched
+long long launches_total();
+cudaError_t launch_init_labels(const int* init, int* a, int* b, long long n, Counters* ctr,
+                               const DeviceInfo& di, cudaStream_t s);
+long long hub_grid_size(const Tuning& t, const DeviceInfo& di);
+
+// split_kernels.cu
+cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels,
+                         const int* work, Counters* ctr, int* parent, int* out, const Tuning& t,
+                         const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_renumber(const int* rep, int* out, long long n, int* rank, unsigned long long* block_sums,
+                            long long nblocks_cap, unsigned long long* k_dev, const DeviceInfo& di,
+                            cudaStream_t s);
+long long renumber_blocks(long long n);
+
+// modularity_kernels.cu
+struct ModSums {
+  unsigned long long two_m;
+  unsigned long long s1;
+  unsigned long long s2_lo, s2_hi;
+};
+cudaError_t launch_modularity(const long long* off, const int* col, const int* w, long long n,
+                              const int* labels, const int* work, Counters* ctr,
+                              unsigned long long* sigma, unsigned long long* partials, long long nparts,
+                              ModSums* out, const Tuning& t, const DeviceInfo& di, cudaStream_t s);
+long long modularity_partials(const DeviceInfo& di);
+
+}  // namespace gsl

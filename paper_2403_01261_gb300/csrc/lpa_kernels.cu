@@ -1,0 +1,642 @@
+// lpa_kernels.cu -- the label-propagation sweep of GSL-LPA on sm_103a.
+//
+// One sweep applies Eq. 2 (C_i = argmax_c sum_{j in J_i, C_j = c} w_ij,
+// scanCommunities() of Algorithm 3 skipping j == i) to every vertex of the
+// frontier, with ties going to the smallest label.  Integer weights make the
+// per-label sums exact and the argmax a max over the packed 64-bit key
+// (sum << 32 | ~label), so the result does not depend on the order in which
+// threads add: the synchronous sweep is deterministic.
+//
+// Work is split by degree class (binning pass below):
+//   d <= 32     lane groups of G = 1..32 lanes, one vertex per group; equal
+//               labels are found with __match_any_sync and summed with
+//               __popc / __reduce_add_sync; the argmax is two __reduce_max.
+//   d <= 128    one warp per vertex; per-warp open-addressing table in
+//               shared memory.
+//   d <= 4096   one block per vertex; block table in shared memory.
+//   larger      one block per vertex; table in a global-memory region owned
+//               by the block (L2 resident for all but the largest hubs).
+// The hash kernels never scan their table: every insert returns the new sum
+// of its label, each thread keeps the largest packed key it has produced,
+// and the final sum of every label is produced by the thread that added
+// last, so the block maximum of those keys is the argmax.
+//
+// Pruning (lpaMove(): a processed vertex is re-marked when a neighbour
+// changes): a vertex whose label changes sets the next-frontier flag of each
+// neighbour and, in synchronous mode, of itself (the double buffer then
+// stays consistent for unprocessed vertices).  Eq. 2 depends on neighbour
+// labels only, so skipping the other vertices gives the same labels as a
+// full sweep.
+#include <atomic>
+
+#include "kernels.h"
+
+namespace gsl {
+
+namespace {
+
+constexpr unsigned EMPTY = 0xFFFFFFFFu;   // labels are < 2^31, never EMPTY
+constexpr int PROBE_CAP = 1 << 24;        // bound on open-addressing probes
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long pack_key(unsigned sum, int lbl) {
+  return ((unsigned long long)sum << 32) | (unsigned long long)(~(unsigned)lbl);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(FULL, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+
+// Block-wide maximum; every thread must call; returns the result to all.
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* red) {
+  x = warp_max_u64(x);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) red[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long y = lane < nw ? red[lane] : 0ull;
+    y = warp_max_u64(y);
+    if (lane == 0) red[32] = y;
+  }
+  __syncthreads();
+  const unsigned long long r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// Adds the per-thread sweep statistics of the whole block to the counters.
+__device__ __forceinline__ void flush_counters(Counters* ctr, int cls, unsigned long long dn,
+                                               unsigned long long scanned) {
+  __shared__ unsigned long long acc[2];
+  if (threadIdx.x == 0) { acc[0] = 0; acc[1] = 0; }
+  __syncthreads();
+  dn = warp_sum_u64(dn);
+  scanned = warp_sum_u64(scanned);
+  if ((threadIdx.x & 31) == 0) {
+    if (dn) atomicAdd(&acc[0], dn);
+    if (scanned) atomicAdd(&acc[1], scanned);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (acc[0]) atomicAdd(&ctr->dn, acc[0]);
+    if (acc[1]) {
+      atomicAdd(&ctr->scanned, acc[1]);
+      atomicAdd(&ctr->cls_scanned[cls], acc[1]);
+    }
+  }
+}
+
+// Open-addressing insert (linear probing, cap slots, any cap).  Returns the
+// label's new sum, or 0 if the probe bound was hit.
+template <bool GLOBAL>
+__device__ __forceinline__ unsigned table_add(unsigned* keys, unsigned* vals, unsigned cap, unsigned lbl,
+                                              unsigned c, int* err) {
+  unsigned h = __umulhi(hash32(lbl), cap);
+  for (int p = 0; p < PROBE_CAP; ++p) {
+    unsigned k = GLOBAL ? __ldcg(keys + h) : *(volatile unsigned*)(keys + h);
+    if (k == EMPTY) {
+      k = atomicCAS(keys + h, EMPTY, lbl);
+      if (k == EMPTY) k = lbl;
+    }
+    if (k == lbl) return atomicAdd(vals + h, c) + c;
+    if (++h == cap) h = 0;
+  }
+  raise_err(err, ERRBIT_TIMEOUT);
+  return 0;
+}
+
+// Loads entry e of a row: neighbour j (or -1 when e is past the row end or
+// j is out of range) and its weight.
+template <bool WEIGHTED>
+__device__ __forceinline__ void load_entry(const SweepArgs& a, long long s, int d, int e, int& j, int& wt) {
+  j = -1;
+  wt = 0;
+  if (e < d) {
+    j = ld_stream(a.col + s + e);
+    wt = WEIGHTED ? ld_stream(a.w + s + e) : 1;
+    if ((unsigned)j >= (unsigned)a.n) {
+      raise_err(&a.ctr->err, ERRBIT_INVALID);
+      j = -1;
+    } else if (WEIGHTED && a.check && wt <= 0) {
+      raise_err(&a.ctr->err, ERRBIT_INVALID);
+      j = -1;
+    }
+  }
+}
+
+template <bool ASYNC>
+__device__ __forceinline__ int gather_label(const SweepArgs& a, int j) {
+  if (a.ident) return j;
+  return ASYNC ? ld_label_rw(a.prev + j) : ld_label_ro(a.prev + j);
+}
+
+template <bool ASYNC>
+__device__ __forceinline__ int own_label(const SweepArgs& a, int v) {
+  if (a.ident) return v;
+  return ASYNC ? ld_label_rw(a.prev + v) : a.prev[v];
+}
+
+template <bool ASYNC>
+__device__ __forceinline__ void store_label(const SweepArgs& a, int v, int nl, bool changed) {
+  if (!ASYNC) a.next[v] = nl;             // Jacobi: C^t is written for every processed vertex
+  else if (changed) __stcg(a.next + v, nl);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Static classification of all vertices: class totals, region starts, max
+// degree; validates the offsets array.
+__global__ void class_histogram_kernel(const long long* __restrict__ off, long long n, long long nnz, int warp_max,
+                                       int blk_max, Counters* ctr) {
+  __shared__ unsigned long long hist[NCLASS];
+  __shared__ long long maxd;
+  __shared__ int bad;
+  if (threadIdx.x < NCLASS) hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0) { maxd = 0; bad = 0; }
+  __syncthreads();
+  long long lmax = 0;
+  int lbad = 0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const long long s = off[v], e = off[v + 1];
+    if (s < 0 || e < s || e > nnz) { lbad |= ERRBIT_INVALID; continue; }
+    const long long d = e - s;
+    if (d >= (1ll << 31)) { lbad |= ERRBIT_OVERFLOW; continue; }
+    lmax = d > lmax ? d : lmax;
+    const int c = degree_class(d, warp_max, blk_max);
+    if (c >= 0) atomicAdd(&hist[c], 1ull);
+    if (v == 0 && s != 0) lbad |= ERRBIT_INVALID;
+    if (v == n - 1 && e != nnz) lbad |= ERRBIT_INVALID;
+  }
+  if (lmax) atomicMax(&maxd, lmax);
+  if (lbad) atomicOr(&bad, lbad);
+  __syncthreads();
+  if (threadIdx.x < NCLASS && hist[threadIdx.x]) atomicAdd(&ctr->cls_total[threadIdx.x], hist[threadIdx.x]);
+  if (threadIdx.x == 0) {
+    if (maxd) atomicMax(&ctr->max_degree, maxd);
+    if (bad) atomicOr(&ctr->err, bad);
+  }
+}
+
+__global__ void class_starts_kernel(Counters* ctr) {
+  unsigned long long run = 0;
+  for (int c = 0; c < NCLASS; ++c) {
+    ctr->cls_start[c] = run;
+    run += ctr->cls_total[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Frontier binning: every vertex with its flag set (or every vertex when
+// all_active) is appended to its class region; the flag is cleared, which
+// leaves the flag array zeroed for reuse as the frontier after next.
+constexpr int BIN_ITEMS = 8;
+
+__global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ off, long long n,
+                                                   unsigned char* __restrict__ fcur, int all_active, int warp_max,
+                                                   int blk_max, int* __restrict__ work, Counters* ctr) {
+  __shared__ unsigned cnt[NCLASS];
+  __shared__ unsigned base[NCLASS];
+  const long long tile = (long long)blockDim.x * BIN_ITEMS;
+  for (long long t0 = (long long)blockIdx.x * tile; t0 < n; t0 += (long long)gridDim.x * tile) {
+    if (threadIdx.x < NCLASS) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int cls[BIN_ITEMS];
+    unsigned pos[BIN_ITEMS];
+#pragma unroll
+    for (int k = 0; k < BIN_ITEMS; ++k) {
+      const long long v = t0 + (long long)k * blockDim.x + threadIdx.x;
+      cls[k] = -1;
+      if (v < n) {
+        bool act = all_active != 0;
+        if (!act && fcur[v]) { act = true; fcur[v] = 0; }
+        if (act) cls[k] = degree_class(off[v + 1] - off[v], warp_max, blk_max);
+      }
+      if (cls[k] >= 0) pos[k] = atomicAdd(&cnt[cls[k]], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < NCLASS) base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&ctr->cls_count[threadIdx.x], cnt[threadIdx.x]) : 0u;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BIN_ITEMS; ++k) {
+      if (cls[k] >= 0) {
+        const long long v = t0 + (long long)k * blockDim.x + threadIdx.x;
+        work[ctr->cls_start[cls[k]] + base[cls[k]] + pos[k]] = (int)v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void init_labels_kernel(const int* __restrict__ init, int* __restrict__ a, int* __restrict__ b, long long n,
+                                   Counters* ctr) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    int x = (int)v;
+    if (init) {
+      x = init[v];
+      if (x < 0 || x >= n) {
+        raise_err(&ctr->err, ERRBIT_INVALID);
+        x = (int)v;
+      }
+    }
+    a[v] = x;
+    if (b) b[v] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Classes 0..5: G lanes per vertex, 32/G vertices per warp per step.
+template <int G, bool WEIGHTED, bool ASYNC>
+__global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) {
+  const unsigned cnt = a.ctr->cls_count[cls];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const int gbase = lane & ~(G - 1);
+  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
+  constexpr int PER_WARP = 32 / G;
+  const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_dn = 0, my_scan = 0;
+  for (long long wb = warp_id * PER_WARP; wb < (long long)cnt; wb += nwarps * PER_WARP) {
+    const long long item = wb + lane / G;
+    const bool has = item < (long long)cnt;
+    int v = 0;
+    long long s = 0;
+    int d = 0;
+    if (has) {
+      v = work[item];
+      s = a.off[v];
+      d = (int)(a.off[v + 1] - s);
+    }
+    int j, wt;
+    load_entry<WEIGHTED>(a, s, d, gl, j, wt);
+    const bool nb = j >= 0;
+    const bool valid = nb && j != v;       // scanCommunities skips j == i
+    const int lbl = valid ? gather_label<ASYNC>(a, j) : -1;
+    if (WEIGHTED && a.check) {
+      unsigned long long ws = nb ? (unsigned long long)wt : 0ull;
+#pragma unroll
+      for (int o = G / 2; o >= 1; o >>= 1) ws += __shfl_xor_sync(FULL, ws, o);
+      if (gl == 0 && has && ws >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+    }
+    const unsigned m = __match_any_sync(FULL, lbl) & gmask;
+    const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)wt) : (unsigned)__popc(m);
+    const unsigned cc = valid ? c : 0u;
+    const unsigned mc = __reduce_max_sync(gmask, cc);
+    const unsigned cand = (valid && cc == mc) ? ~(unsigned)lbl : 0u;
+    const unsigned binv = __reduce_max_sync(gmask, cand);
+    bool changed = false;
+    if (has && gl == 0) {
+      const int old = own_label<ASYNC>(a, v);
+      const int nl = mc ? (int)~binv : old;
+      changed = nl != old;
+      store_label<ASYNC>(a, v, nl, changed);
+      my_scan += (unsigned long long)d;
+      my_dn += changed ? 1ull : 0ull;
+    }
+    if (a.mark) {
+      const unsigned chm = __ballot_sync(FULL, changed);
+      if ((chm >> gbase) & 1u) {
+        if (nb) a.fnext[j] = 1;
+        if (!ASYNC && gl == 0) a.fnext[v] = 1;
+      }
+    }
+  }
+  flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// ---------------------------------------------------------------------------
+// Sweep 1 from the identity labelling on a row whose columns are strictly
+// increasing: every neighbour id is its own label and occurs once, so the
+// sum of label j is w_ij and the argmax is the max of (w_ij, ~j).  Returns
+// false if the row is not strictly increasing (the caller then hashes).
+// `best` is the per-thread partial key; `wsum` the per-thread weight sum.
+template <bool WEIGHTED>
+__device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, long long s, int d, int tid, int nthreads,
+                                                  unsigned long long& best, unsigned long long& wsum) {
+  bool sorted = true;
+  for (int e0 = (tid & ~31); e0 < d; e0 += (nthreads & ~31)) {
+    const int lane = tid & 31;
+    int j, wt;
+    load_entry<WEIGHTED>(a, s, d, e0 + lane, j, wt);
+    int nxt = __shfl_down_sync(FULL, j, 1);
+    if (lane == 31 && e0 + 32 < d) nxt = ld_stream(a.col + s + e0 + 32);
+    if (j >= 0 && e0 + lane + 1 < d && !(j < nxt)) sorted = false;
+    if (j < 0 && e0 + lane < d) sorted = false;      // invalid entry: let the hash path handle it
+    if (j >= 0) {
+      wsum += (unsigned long long)wt;
+      if (j != v) {
+        const unsigned long long k = pack_key((unsigned)wt, j);
+        best = k > best ? k : best;
+      }
+    }
+  }
+  return sorted;
+}
+
+// ---------------------------------------------------------------------------
+// Class 6: one warp per vertex, shared-memory table of `capw` slots per warp.
+template <bool WEIGHTED, bool ASYNC>
+__global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int capw) {
+  extern __shared__ unsigned smem_w[];
+  const int lane = threadIdx.x & 31;
+  unsigned* keys = smem_w + (size_t)(threadIdx.x >> 5) * 2 * capw;
+  unsigned* vals = keys + capw;
+  const unsigned cnt = a.ctr->cls_count[CLS_WARP];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[CLS_WARP];
+  const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_dn = 0, my_scan = 0;
+  for (long long item = warp_id; item < (long long)cnt; item += nwarps) {
+    const int v = work[item];
+    const long long s = a.off[v];
+    const int d = (int)(a.off[v + 1] - s);
+    unsigned long long best = 0, wsum = 0;
+    bool sorted = false;
+    if (a.ident && !ASYNC) sorted = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, best, wsum));
+    if (!sorted) {
+      best = 0;
+      wsum = 0;
+      const unsigned cap = (unsigned)(2 * d) < (unsigned)capw ? (unsigned)(2 * d) : (unsigned)capw;
+      for (unsigned k = lane; k < cap; k += 32) { keys[k] = EMPTY; vals[k] = 0; }
+      __syncwarp();
+      for (int e0 = 0; e0 < d; e0 += 32) {
+        int j, wt;
+        load_entry<WEIGHTED>(a, s, d, e0 + lane, j, wt);
+        const bool valid = j >= 0 && j != v;
+        if (j >= 0) wsum += (unsigned long long)wt;
+        const int lbl = valid ? gather_label<ASYNC>(a, j) : -1;
+        const unsigned m = __match_any_sync(FULL, lbl);
+        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)wt) : (unsigned)__popc(m);
+        if (valid && (m & lanemask_lt()) == 0) {
+          const unsigned sum = table_add<false>(keys, vals, cap, (unsigned)lbl, c, &a.ctr->err);
+          const unsigned long long k = pack_key(sum, lbl);
+          best = k > best ? k : best;
+        }
+      }
+      __syncwarp();
+    }
+    best = warp_max_u64(best);
+    if (WEIGHTED && a.check) {
+      wsum = warp_sum_u64(wsum);
+      if (lane == 0 && wsum >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+    }
+    const int old = own_label<ASYNC>(a, v);
+    const int nl = best ? (int)~(unsigned)best : old;
+    const bool changed = nl != old;
+    if (lane == 0) {
+      store_label<ASYNC>(a, v, nl, changed);
+      my_scan += (unsigned long long)d;
+      my_dn += changed ? 1ull : 0ull;
+    }
+    if (changed && a.mark) {
+      for (int e = lane; e < d; e += 32) {
+        const int j = ld_stream(a.col + s + e);
+        if ((unsigned)j < (unsigned)a.n) a.fnext[j] = 1;
+      }
+      if (!ASYNC && lane == 0) a.fnext[v] = 1;
+    }
+  }
+  flush_counters(a.ctr, CLS_WARP, my_dn, my_scan);
+}
+
+// ---------------------------------------------------------------------------
+// Classes 7 and 8: one block per vertex.  GLOBAL selects the table: shared
+// memory (class 7, `cap_slots` slots of dynamic shared memory) or the
+// block's own region of the global hub tables (class 8).
+template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
+__global__ void __launch_bounds__(1024) sweep_block_kernel(SweepArgs a, int cls, unsigned cap_slots) {
+  extern __shared__ unsigned smem_b[];
+  __shared__ unsigned long long red[33];
+  __shared__ int s_changed;
+  __shared__ unsigned long long s_wtot;
+  unsigned* keys;
+  unsigned* vals;
+  if (GLOBAL) {
+    keys = a.hub_keys + (long long)blockIdx.x * a.hub_region;
+    vals = a.hub_vals + (long long)blockIdx.x * a.hub_region;
+  } else {
+    keys = smem_b;
+    vals = smem_b + cap_slots;
+  }
+  const unsigned cnt = a.ctr->cls_count[cls];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const int lane = threadIdx.x & 31;
+  const int nthreads = blockDim.x;
+  unsigned long long my_dn = 0, my_scan = 0;
+  for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
+    const int v = work[item];
+    const long long s = a.off[v];
+    const int d = (int)(a.off[v + 1] - s);
+    unsigned long long best = 0, wsum = 0;
+    int sorted = 0;
+    if (a.ident && !ASYNC) sorted = __syncthreads_and(ident_sorted_pass<WEIGHTED>(a, v, s, d, threadIdx.x, nthreads, best, wsum));
+    if (!sorted) {
+      best = 0;
+      wsum = 0;
+      const long long want = 2ll * d;
+      const unsigned cap = (unsigned)(want < (long long)cap_slots ? want : (long long)cap_slots);
+      for (unsigned k = threadIdx.x; k < cap; k += nthreads) { keys[k] = EMPTY; vals[k] = 0; }
+      __syncthreads();
+      // each warp takes 32-entry chunks; two chunks in flight per step
+      const int wid = threadIdx.x >> 5, nw = nthreads >> 5;
+      for (int e0 = wid * 64; e0 < d; e0 += nw * 64) {
+        int j0, w0, j1, w1;
+        load_entry<WEIGHTED>(a, s, d, e0 + lane, j0, w0);
+        load_entry<WEIGHTED>(a, s, d, e0 + 32 + lane, j1, w1);
+        const bool v0 = j0 >= 0 && j0 != v, v1 = j1 >= 0 && j1 != v;
+        if (j0 >= 0) wsum += (unsigned long long)w0;
+        if (j1 >= 0) wsum += (unsigned long long)w1;
+        const int l0 = v0 ? gather_label<ASYNC>(a, j0) : -1;
+        const int l1 = v1 ? gather_label<ASYNC>(a, j1) : -1;
+        const unsigned m0 = __match_any_sync(FULL, l0);
+        const unsigned c0 = WEIGHTED ? __reduce_add_sync(m0, (unsigned)w0) : (unsigned)__popc(m0);
+        if (v0 && (m0 & lanemask_lt()) == 0) {
+          const unsigned sum = table_add<GLOBAL>(keys, vals, cap, (unsigned)l0, c0, &a.ctr->err);
+          const unsigned long long k = pack_key(sum, l0);
+          best = k > best ? k : best;
+        }
+        const unsigned m1 = __match_any_sync(FULL, l1);
+        const unsigned c1 = WEIGHTED ? __reduce_add_sync(m1, (unsigned)w1) : (unsigned)__popc(m1);
+        if (v1 && (m1 & lanemask_lt()) == 0) {
+          const unsigned sum = table_add<GLOBAL>(keys, vals, cap, (unsigned)l1, c1, &a.ctr->err);
+          const unsigned long long k = pack_key(sum, l1);
+          best = k > best ? k : best;
+        }
+      }
+    }
+    best = block_max_u64(best, red);
+    if (WEIGHTED && a.check) {
+      wsum = warp_sum_u64(wsum);
+      if (threadIdx.x == 0) s_wtot = 0;
+      __syncthreads();
+      if (lane == 0 && wsum) atomicAdd(&s_wtot, wsum);
+      __syncthreads();
+      if (threadIdx.x == 0 && s_wtot >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+    }
+    if (threadIdx.x == 0) {
+      const int old = own_label<ASYNC>(a, v);
+      const int nl = best ? (int)~(unsigned)best : old;
+      const bool changed = nl != old;
+      store_label<ASYNC>(a, v, nl, changed);
+      my_scan += (unsigned long long)d;
+      my_dn += changed ? 1ull : 0ull;
+      s_changed = changed;
+    }
+    __syncthreads();
+    if (s_changed && a.mark) {
+      for (int e = threadIdx.x; e < d; e += nthreads) {
+        const int j = ld_stream(a.col + s + e);
+        if ((unsigned)j < (unsigned)a.n) a.fnext[j] = 1;
+      }
+      if (!ASYNC && threadIdx.x == 0) a.fnext[v] = 1;
+    }
+    __syncthreads();
+  }
+  flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+namespace {
+template <typename K>
+int occupancy_grid(K kernel, int block, size_t smem, const DeviceInfo& di) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * di.sm_count;
+}
+
+int warp_cap(const Tuning& t) { return (int)next_pow2((unsigned)(2 * t.warp_max)); }
+int block_cap(const Tuning& t) { return 2 * t.blk_max; }
+
+template <bool W, bool A>
+cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
+  switch (cls) {
+#define GSL_LAUNCH_GROUP(G, CLS)                                                                 \
+  case CLS: {                                                                                    \
+    static int grid = 0;                                                                         \
+    if (!grid) grid = occupancy_grid(sweep_group_kernel<G, W, A>, t.group_block, 0, di);         \
+    sweep_group_kernel<G, W, A><<<grid, t.group_block, 0, s>>>(a, CLS);                          \
+    break;                                                                                       \
+  }
+    GSL_LAUNCH_GROUP(1, 0)
+    GSL_LAUNCH_GROUP(2, 1)
+    GSL_LAUNCH_GROUP(4, 2)
+    GSL_LAUNCH_GROUP(8, 3)
+    GSL_LAUNCH_GROUP(16, 4)
+    GSL_LAUNCH_GROUP(32, 5)
+#undef GSL_LAUNCH_GROUP
+    case CLS_WARP: {
+      const int capw = warp_cap(t);
+      const size_t smem = (size_t)(t.warp_block / 32) * 2 * capw * sizeof(unsigned);
+      static int grid = 0;
+      static size_t grid_smem = 0;
+      if (!grid || grid_smem != smem) {
+        cudaFuncSetAttribute(sweep_warp_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        grid = occupancy_grid(sweep_warp_kernel<W, A>, t.warp_block, smem, di);
+        grid_smem = smem;
+      }
+      sweep_warp_kernel<W, A><<<grid, t.warp_block, smem, s>>>(a, capw);
+      break;
+    }
+    case CLS_BLOCK: {
+      const int capb = block_cap(t);
+      const size_t smem = (size_t)2 * capb * sizeof(unsigned);
+      static int grid = 0;
+      static size_t grid_smem = 0;
+      if (!grid || grid_smem != smem) {
+        cudaFuncSetAttribute(sweep_block_kernel<W, A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        grid = occupancy_grid(sweep_block_kernel<W, A, false>, t.blk_block, smem, di);
+        grid_smem = smem;
+      }
+      sweep_block_kernel<W, A, false><<<grid, t.blk_block, smem, s>>>(a, CLS_BLOCK, (unsigned)capb);
+      break;
+    }
+    case CLS_HUB: {
+      const int grid = (int)hub_grid_size(t, di);
+      sweep_block_kernel<W, A, true><<<grid, t.hub_block, 0, s>>>(a, CLS_HUB, (unsigned)a.hub_region);
+      break;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+}  // namespace
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+long long hub_grid_size(const Tuning& t, const DeviceInfo& di) { return t.hub_grid > 0 ? t.hub_grid : di.sm_count; }
+
+cudaError_t launch_class_histogram(const long long* off, long long n, long long nnz, const Tuning& t, Counters* ctr,
+                                   const DeviceInfo& di, cudaStream_t s) {
+  if (n > 0) {
+    long long blocks = (n + 255) / 256;
+    const long long cap = 8ll * di.sm_count;
+    class_histogram_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, nnz, t.warp_max, t.blk_max, ctr);
+  }
+  class_starts_kernel<<<1, 1, 0, s>>>(ctr);
+  count_launches(n > 0 ? 2 : 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, int all_active, const Tuning& t,
+                       int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long tile = 256ll * BIN_ITEMS;
+  long long blocks = (n + tile - 1) / tile;
+  const long long cap = 8ll * di.sm_count;
+  bin_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, fcur, all_active, t.warp_max, t.blk_max, work,
+                                                                 ctr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_labels(const int* init, int* a, int* b, long long n, Counters* ctr, const DeviceInfo& di,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  const long long cap = 8ll * di.sm_count;
+  init_labels_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(init, a, b, n, ctr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool async_mode, const Tuning& t,
+                               const DeviceInfo& di, cudaStream_t s) {
+  if (weighted)
+    return async_mode ? launch_sweep_t<true, true>(a, cls, t, di, s) : launch_sweep_t<true, false>(a, cls, t, di, s);
+  return async_mode ? launch_sweep_t<false, true>(a, cls, t, di, s) : launch_sweep_t<false, false>(a, cls, t, di, s);
+}
+
+cudaError_t launch_sweep(const SweepArgs& a, bool weighted, bool async_mode, const Tuning& t, const DeviceInfo& di,
+                         cudaStream_t s) {
+  for (int c = 0; c < NCLASS; ++c)
+    if (cudaError_t e = launch_sweep_class(a, c, weighted, async_mode, t, di, s)) return e;
+  return cudaSuccess;
+}
+
+}  // namespace gsl

@@ -1,0 +1,241 @@
+// split_kernels.cu -- split last (Algorithm 2) and label renumbering on sm_103a.
+//
+// Algorithm 2 labels every connected piece of every community with the
+// vertex its BFS started from; scanning start vertices in ascending order
+// makes that the smallest vertex of the piece.  Here the pieces are found
+// as the connected components of the subgraph of edges (u, j) with
+// C[u] == C[j], by lock-free union-find instead of one BFS per piece:
+//   - parent[v] <= v at all times; a union links the larger of two roots
+//     below the smaller with atomicCAS, so the root of every tree is the
+//     smallest vertex of its component;
+//   - find follows parents with path halving (benign racy stores: every
+//     value written is an ancestor of the vertex);
+//   - each undirected edge is offered once, from its larger endpoint.
+// All loops are bounded (parents strictly decrease along a path and a
+// failed CAS strictly lowers the root being linked); the bound is a safety
+// net that raises ERRBIT_TIMEOUT.
+#include "kernels.h"
+
+namespace gsl {
+
+namespace {
+
+constexpr int UF_CAP = 1 << 26;
+
+__device__ __forceinline__ int uf_find(int* p, int x, int* err) {
+  for (int it = 0; it < UF_CAP; ++it) {
+    const int px = __ldcg(p + x);
+    if (px == x) return x;
+    const int ppx = __ldcg(p + px);
+    if (ppx != px) __stcg(p + x, ppx);
+    x = ppx;
+  }
+  raise_err(err, ERRBIT_TIMEOUT);
+  return x;
+}
+
+__device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err) {
+  for (int it = 0; it < UF_CAP; ++it) {
+    a = uf_find(p, a, err);
+    b = uf_find(p, b, err);
+    if (a == b) return;
+    const int hi = a > b ? a : b, lo = a > b ? b : a;
+    const int old = atomicCAS(p + hi, hi, lo);
+    if (old == hi) return;
+    a = old;   // hi got a parent meanwhile: continue from it
+    b = lo;
+  }
+  raise_err(err, ERRBIT_TIMEOUT);
+}
+
+// Offers the intra-community edges (u, j), j < u, of one row slice to the
+// union-find.
+__device__ __forceinline__ void hook_entry(const int* col, const int* labels, int* p, long long n, int u, int cu,
+                                           long long e, int* err) {
+  const int j = ld_stream(col + e);
+  if ((unsigned)j >= (unsigned)n) {
+    raise_err(err, ERRBIT_INVALID);
+    return;
+  }
+  if (j < u && ld_label_ro(labels + j) == cu) uf_unite(p, u, j, err);
+}
+
+}  // namespace
+
+__global__ void init_parent_kernel(int* __restrict__ p, long long n) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    p[v] = (int)v;
+}
+
+// Classes 0..6: G lanes per vertex, looping over the row in strides of G.
+template <int G>
+__global__ void __launch_bounds__(256) hook_group_kernel(const long long* __restrict__ off, const int* __restrict__ col,
+                                                          const int* __restrict__ labels, int* p, long long n,
+                                                          const int* __restrict__ work, Counters* ctr, int cls) {
+  const unsigned cnt = (unsigned)ctr->cls_total[cls];
+  const int* w = work + ctr->cls_start[cls];
+  const int gl = threadIdx.x & (G - 1);
+  const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const long long ng = ((long long)gridDim.x * blockDim.x) / G;
+  for (long long item = gid; item < (long long)cnt; item += ng) {
+    const int u = w[item];
+    const long long s = off[u], e = off[u + 1];
+    const int cu = labels[u];
+    for (long long k = s + gl; k < e; k += G) hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
+  }
+}
+
+// Classes 7..8: one block per vertex.
+__global__ void __launch_bounds__(512) hook_block_kernel(const long long* __restrict__ off, const int* __restrict__ col,
+                                                          const int* __restrict__ labels, int* p, long long n,
+                                                          const int* __restrict__ work, Counters* ctr, int cls) {
+  const unsigned cnt = (unsigned)ctr->cls_total[cls];
+  const int* w = work + ctr->cls_start[cls];
+  for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
+    const int u = w[item];
+    const long long s = off[u], e = off[u + 1];
+    const int cu = labels[u];
+    for (long long k = s + threadIdx.x; k < e; k += blockDim.x) hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
+  }
+}
+
+__global__ void compress_kernel(int* p, int* __restrict__ out, long long n, Counters* ctr) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    out[v] = uf_find(p, (int)v, &ctr->err);
+}
+
+// ---------------------------------------------------------------- renumber
+// rank of every representative (out[v] == v) among all representatives,
+// then out[v] = rank[out[v]]: pieces numbered 0..k-1 by smallest vertex.
+constexpr int RN_THREADS = 256;
+constexpr int RN_ITEMS = 8;
+constexpr long long RN_TILE = (long long)RN_THREADS * RN_ITEMS;
+
+__global__ void __launch_bounds__(RN_THREADS) rn_count_kernel(const int* __restrict__ rep, long long n,
+                                                               unsigned long long* __restrict__ block_sums) {
+  __shared__ unsigned long long acc;
+  if (threadIdx.x == 0) acc = 0;
+  __syncthreads();
+  const long long t0 = (long long)blockIdx.x * RN_TILE;
+  unsigned c = 0;
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    const long long v = t0 + (long long)threadIdx.x * RN_ITEMS + k;
+    if (v < n && rep[v] == (int)v) ++c;
+  }
+  atomicAdd(&acc, (unsigned long long)c);
+  __syncthreads();
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(1024) rn_scan_kernel(unsigned long long* block_sums, long long nb,
+                                                        unsigned long long* total) {
+  __shared__ unsigned long long buf[1024];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long long b0 = 0; b0 < nb; b0 += 1024) {
+    const long long b = b0 + threadIdx.x;
+    const unsigned long long x = b < nb ? block_sums[b] : 0ull;
+    buf[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan
+      const unsigned long long y = threadIdx.x >= (unsigned)o ? buf[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      buf[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (b < nb) block_sums[b] = carry + buf[threadIdx.x] - x;   // exclusive
+    __syncthreads();
+    if (threadIdx.x == 0) carry += buf[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(RN_THREADS) rn_rank_kernel(const int* __restrict__ rep, long long n,
+                                                              const unsigned long long* __restrict__ block_sums,
+                                                              int* __restrict__ rank) {
+  __shared__ unsigned warp_tot[RN_THREADS / 32];
+  const long long t0 = (long long)blockIdx.x * RN_TILE;
+  unsigned flags = 0, c = 0;
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    const long long v = t0 + (long long)threadIdx.x * RN_ITEMS + k;
+    if (v < n && rep[v] == (int)v) { flags |= 1u << k; ++c; }
+  }
+  // exclusive scan of c over the block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned incl = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  unsigned wbase = 0;
+  for (int w = 0; w < wid; ++w) wbase += warp_tot[w];
+  unsigned long long r = block_sums[blockIdx.x] + wbase + incl - c;
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    if (flags >> k & 1u) {
+      const long long v = t0 + (long long)threadIdx.x * RN_ITEMS + k;
+      rank[v] = (int)r++;
+    }
+  }
+}
+
+__global__ void rn_apply_kernel(const int* __restrict__ rep, int* __restrict__ out, const int* __restrict__ rank,
+                                long long n) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    out[v] = rank[rep[v]];
+}
+
+// ---------------------------------------------------------------- launchers
+namespace {
+int grid_for(long long items, int block, const DeviceInfo& di, int per_sm = 8) {
+  long long b = (items + block - 1) / block;
+  const long long cap = (long long)per_sm * di.sm_count;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+}  // namespace
+
+cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels, const int* work,
+                         Counters* ctr, int* parent, int* out, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
+  (void)t;
+  if (n <= 0) return cudaSuccess;
+  init_parent_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, n);
+  const int g = 8 * di.sm_count;
+  hook_group_kernel<1><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 0);
+  hook_group_kernel<2><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 1);
+  hook_group_kernel<4><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 2);
+  hook_group_kernel<8><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 3);
+  hook_group_kernel<16><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 4);
+  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 5);
+  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP);
+  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_BLOCK);
+  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_HUB);
+  compress_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr);
+  count_launches(11);
+  return cudaGetLastError();
+}
+
+long long renumber_blocks(long long n) { return (n + RN_TILE - 1) / RN_TILE; }
+
+cudaError_t launch_renumber(const int* rep, int* out, long long n, int* rank, unsigned long long* block_sums,
+                            long long nblocks_cap, unsigned long long* k_dev, const DeviceInfo& di, cudaStream_t s) {
+  const long long nb = renumber_blocks(n);
+  if (nb > nblocks_cap) return cudaErrorInvalidValue;
+  if (n <= 0) {
+    cudaMemsetAsync(k_dev, 0, sizeof(unsigned long long), s);
+    return cudaGetLastError();
+  }
+  rn_count_kernel<<<(int)nb, RN_THREADS, 0, s>>>(rep, n, block_sums);
+  rn_scan_kernel<<<1, 1024, 0, s>>>(block_sums, nb, k_dev);
+  count_launches(2);
+  if (!out) return cudaGetLastError();   // count only
+  rn_rank_kernel<<<(int)nb, RN_THREADS, 0, s>>>(rep, n, block_sums, rank);
+  rn_apply_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(rep, out, rank, n);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace gsl
