@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""GSL-LPA benchmark: LPA + split throughput (|E|/s) on one GB300 per rank.
+
+Default workload: R-MAT scale 25, edge factor 24 (a, b, c, d = 0.57, 0.19,
+0.19, 0.05), symmetrised, deduplicated, self-loops dropped, vertex ids
+randomly permuted, unit weights; synchronous LPA, tolerance 0.05, at most 20
+sweeps, then the split.  |E| counts directed CSR entries (both directions of
+every edge).  One step = one gsl_gsllpa call (all sweeps + split) on the
+resident graph.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own copy of the graph on its own
+GPU (the single-graph path does not shard; replicas only, no collective on
+the data path); value = all ranks' entries / max-over-ranks step time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LPA+split |E|/s on R-MAT-25 (sync, tol 0.05, max 20 sweeps)"
+UNIT = "edges/s"
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--scale", type=int, default=25, help="R-MAT scale of the workload")
+    p.add_argument("--edge-factor", type=int, default=24)
+    p.add_argument("--mode", choices=["sync", "async"], default="sync")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-scale", type=int, default=19, help="R-MAT scale of the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cache", default=os.environ.get("GSL_BENCH_CACHE", os.path.join(tempfile.gettempdir(),
+                                                                                    "gsl_bench_cache")))
+    p.add_argument("--profile-json", default="", help="also write the per-slot profile here")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def workload_graph(scale, edge_factor, cache, rank, world):
+    """R-MAT graph, generated once per machine and cached as .npy files."""
+    import numpy as np
+    import inputs as I
+    tag = f"rmat{scale}_ef{edge_factor}_s1"
+    off_p = os.path.join(cache, tag + "_offsets.npy")
+    col_p = os.path.join(cache, tag + "_cols.npy")
+    if rank == 0 and not (os.path.exists(off_p) and os.path.exists(col_p)):
+        os.makedirs(cache, exist_ok=True)
+        t0 = time.time()
+        g = I.rmat(scale, edge_factor, 0.57, 0.19, 0.19, seed=1, permute=True)
+        gen_s = time.time() - t0
+        for p_, a in ((off_p, g.offsets), (col_p, g.cols)):
+            tmp = p_ + f".{os.getpid()}.tmp.npy"
+            np.save(tmp, a)
+            os.replace(tmp, p_)
+        print(f"[bench] generated {g} in {gen_s:.1f}s", file=sys.stderr, flush=True)
+        del g
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    offsets = np.load(off_p, mmap_mode="r")
+    cols = np.load(col_p, mmap_mode="r")
+    return offsets, cols
+
+
+# -------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU side
+def cpu_baseline(scale, edge_factor, tol, max_iters):
+    """The oracle as it stands (single thread): full GSL-LPA (synchronous LPA
+    + BFS split) on a smaller R-MAT of the same generator and parameters."""
+    import inputs as I
+    import oracle as O
+    g = I.rmat(scale, edge_factor, 0.57, 0.19, 0.19, seed=1, permute=True)
+    t0 = time.perf_counter()
+    lab, t, dn = O.lpa_sync(g, tol, max_iters)
+    t1 = time.perf_counter()
+    O.split_bfs(g, lab)
+    t2 = time.perf_counter()
+    return {
+        "value": g.nnz / (t2 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": (f"full oracle GSL-LPA (Jacobi LPA tol {tol} max {max_iters}, then BFS split) on R-MAT scale "
+                   f"{scale} ef {edge_factor}, same generator and seed: n={g.n}, nnz={g.nnz}, {t} sweeps, "
+                   f"lpa {t1 - t0:.2f}s split {t2 - t1:.2f}s; the scale-25 graph exceeds the sample budget"),
+        "host_cores": os.cpu_count(),
+        "seconds": t2 - t0,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401  (builds the oracle)
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(min(args.cpu_scale, 18), args.edge_factor, 0.05, 20)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    value = statistics.median(vals) if vals else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale}-ef{args.edge_factor}", "sample_scale": min(args.cpu_scale, 18),
+                   "tolerance": 0.05, "max_iters": 20, "mode": "sync"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cb["sample"] if cb else ""},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU side
+def dominant_roofline(profile, peaks):
+    slots = [s for s in profile if s["ms"] > 0 and s["bytes"] > 0]
+    if not slots:
+        return None
+    top = max(slots, key=lambda s: s["ms"])
+    achieved = top["bytes"] / (top["ms"] * 1e-3) / 1e9
+    peak, src = peaks
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            from paper_2403_01261_gb300 import _build
+            rec = json.load(open(tpath))
+            if rec.get("source_hash") == _build.source_hash() and top["name"] in rec.get("per_launch", {}):
+                traffic = rec["per_launch"][top["name"]]
+        except Exception:  # noqa: BLE001
+            traffic = None
+    return {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+            "bytes_per_launch": top["bytes"] / max(1, top["launches"]),
+            "ms_per_launch": top["ms"] / max(1, top["launches"]), "launches": top["launches"]}
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except Exception:  # noqa: BLE001
+            pass
+    return 6800.0, "fallback"
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    import paper_2403_01261_gb300 as gsl
+
+    offsets_np, cols_np = workload_graph(args.scale, args.edge_factor, args.cache, rank, world)
+    n = offsets_np.shape[0] - 1
+    nnz = cols_np.shape[0]
+    dev = torch.device("cuda", local)
+    off_h = torch.from_numpy(np.ascontiguousarray(offsets_np)).pin_memory()
+    col_h = torch.from_numpy(np.ascontiguousarray(cols_np)).pin_memory()
+    off = off_h.to(dev)
+    col = col_h.to(dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = gsl.Context(local)
+    mode = 1 if args.mode == "async" else 0
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        ctx.gsllpa(off, col, tolerance=0.05, max_iters=20, mode=mode, out=out)
+    torch.cuda.synchronize(dev)
+
+    # timed region: K steps on resident inputs (cols >> L2, so no flush needed)
+    ctx.set_profiling(True)
+    stats = []
+    launches0 = gsl.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, st = ctx.gsllpa(off, col, tolerance=0.05, max_iters=20, mode=mode, out=out, stats=True)
+            stats.append(st)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    launches = gsl.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the host-buffer entry point (copies inside the region)
+    e2e = None
+    if not args.no_e2e:
+        lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        ctx.gsllpa_host(off_h, col_h, tolerance=0.05, max_iters=20, mode=mode, out=lab_h)   # warm the staging
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            ctx.gsllpa_host(off_h, col_h, tolerance=0.05, max_iters=20, mode=mode, out=lab_h)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = (time.perf_counter() - t0) / args.e2e_steps
+        e2e_ms = max(e0.elapsed_time(e1) / args.e2e_steps, wall * 1e3)
+        if world > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * nnz / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
+               "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms}
+        if mode == 0:
+            assert torch.equal(lab_h, out.cpu()), "host-buffer path disagrees with the device path"
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    st = stats[-1]
+    T = st["iterations"]
+    lpa_ms = statistics.median(s["ms_lpa"] for s in stats)
+    split_ms = statistics.median(s["ms_split"] for s in stats)
+    peak = hbm_peak()
+    roof = dominant_roofline(prof, peak)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_scale, args.edge_factor, 0.05, 20)
+        cpu.pop("seconds", None)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": world * nnz / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale}-ef{args.edge_factor}", "rmat_abcd": [0.57, 0.19, 0.19, 0.05],
+                   "n": n, "nnz": nnz, "tolerance": 0.05, "max_iters": 20, "mode": args.mode, "seed": 1,
+                   "parallelism": f"replicas{world}", "l2": f"inputs larger than L2 (cols {4 * nnz / 1e9:.2f} GB)"},
+        "sweeps": T, "communities": st["communities"], "lpa_ms": lpa_ms, "split_ms": split_ms,
+        "edges_iter_per_s": world * nnz * T / (ms * 1e-3),
+        "edges_scanned_per_s": world * st["edges_scanned"] / (ms * 1e-3),
+        "changed": st["changed"], "active": st["active"],
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    if args.profile_json:
+        with open(args.profile_json, "w") as f:
+            json.dump({"profile": prof, "steps": args.steps, "line": line}, f, indent=1)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -83,12 +83,13 @@ int gsl_ctx_create(gsl_ctx** ctx, int device);
 int gsl_ctx_destroy(gsl_ctx* ctx);
 
 /* Degree-class thresholds of the sweep kernels: vertices of degree
- * 33..warp_max are handled by one warp each (shared-memory table), degree
- * warp_max+1..blk_max by one block each (shared-memory table), and larger
- * degrees by one block each with a global-memory table.  Defaults 128 and
- * 4096.  Requires 32 <= warp_max <= 1024 and warp_max <= blk_max, and
- * 16*blk_max bytes must fit the device's shared memory per block.  Results
- * do not depend on these values. */
+ * 33..warp_max are handled by one warp each, degree warp_max+1..blk_max by
+ * one block each, larger degrees (hubs) by one block each that may go
+ * straight to global-memory tables.  Label sums use shared-memory hash
+ * tables (8 KB per warp, 96 KB per block) and spill to context-owned
+ * global tables when a vertex has more distinct neighbour labels than fit.
+ * Defaults 1024 and 32768.  Requires 32 <= warp_max <= 2^20 and
+ * warp_max <= blk_max.  Results do not depend on these values. */
 int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
 
 /* Label propagation: lpa() of Algorithm 3 without its final split (the

@@ -18,7 +18,7 @@ import threading
 from . import _build
 
 __all__ = ["Stats", "Context", "GslError", "lpa", "split", "modularity", "gsllpa", "gsllpa_host", "library_path",
-           "load", "MODE_SYNC", "MODE_ASYNC"]
+           "load", "kernel_launches", "MODE_SYNC", "MODE_ASYNC"]
 
 MODE_SYNC = 0
 MODE_ASYNC = 1
@@ -39,6 +39,16 @@ class Csr(ctypes.Structure):
                 ("cols", ctypes.c_void_p)]
 
 
+class ProfileSlot(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("kernels", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("vertices", ctypes.c_int64), ("entries", ctypes.c_int64),
+                ("bytes", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("nslots", ctypes.c_int32), ("slot", ProfileSlot * 24)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("changed", ctypes.c_int64 * STATS_SWEEPS), ("active", ctypes.c_int64 * STATS_SWEEPS),
@@ -51,6 +61,11 @@ class Stats(ctypes.Structure):
                 "changed": list(self.changed[:t]), "active": list(self.active[:t]),
                 "edges_scanned": self.edges_scanned, "communities": self.communities,
                 "ms_lpa": self.ms_lpa, "ms_split": self.ms_split}
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(load().gsl_kernel_launches())
 
 
 def library_path() -> str:
@@ -82,7 +97,12 @@ def load():
         lib.gsl_ctx_last_error.restype = ctypes.c_char_p
         lib.gsl_ctx_last_error.argtypes = [P]
         lib.gsl_version.restype = ctypes.c_int
+        lib.gsl_ctx_set_profiling.argtypes = [P, i32]
+        lib.gsl_ctx_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
+        lib.gsl_kernel_launches.restype = i64
+        lib.gsl_kernel_launches.argtypes = []
         for name in ("gsl_ctx_create", "gsl_ctx_destroy", "gsl_ctx_set_tuning", "gsl_lpa", "gsl_split",
+                     "gsl_ctx_set_profiling", "gsl_ctx_get_profile",
                      "gsl_modularity", "gsl_gsllpa", "gsl_gsllpa_host"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -146,6 +166,21 @@ class Context:
 
     def set_tuning(self, warp_max: int, blk_max: int):
         self._raise(self._lib.gsl_ctx_set_tuning(self._h, warp_max, blk_max))
+
+    def set_profiling(self, enable: bool):
+        """Enables (and zeroes) or disables per-slot CUDA-event profiling."""
+        self._raise(self._lib.gsl_ctx_set_profiling(self._h, int(bool(enable))))
+
+    def profile(self):
+        """Per-slot device time, counts and algorithmic bytes since profiling was enabled."""
+        p = Profile()
+        self._raise(self._lib.gsl_ctx_get_profile(self._h, ctypes.byref(p)))
+        out = []
+        for k in range(p.nslots):
+            sl = p.slot[k]
+            out.append({"name": sl.name.decode(), "launches": sl.launches, "kernels": sl.kernels, "ms": sl.ms,
+                        "vertices": sl.vertices, "entries": sl.entries, "bytes": sl.bytes})
+        return out
 
     def lpa(self, offsets, cols, weights=None, labels_init=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC,
             out=None, stream=None, stats=False):

@@ -36,9 +36,10 @@ struct gsl_ctx {
   unsigned long long* partials = nullptr;
   long long cap_partials = 0;
 
-  unsigned* hub_keys = nullptr;
-  unsigned* hub_vals = nullptr;
-  long long cap_hub = 0;           // slots per array
+  unsigned long long* wtab = nullptr;   // warp-kernel fallback tables
+  long long cap_wtab = 0;
+  unsigned long long* btab = nullptr;   // block-kernel fallback tables
+  long long cap_btab = 0;
 
   Counters* ctr = nullptr;         // device
   Counters* ctr_h = nullptr;       // pinned host mirror
@@ -218,18 +219,19 @@ int prepare_graph(gsl_ctx* c, const gsl_csr* g, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   prof_resolve(c);
   if (int r = map_err(c, c->ctr_h->err, "offsets")) return r;
-  if (c->ctr_h->max_degree > c->tune.blk_max) {
-    const long long region = 2 * c->ctr_h->max_degree;
-    const long long need = region * hub_grid_size(c->tune, c->di);
-    long long ck = c->cap_hub, cv = c->cap_hub;
-    if (int r = grow(c, c->hub_keys, ck, need)) return r;
-    if (int r = grow(c, c->hub_vals, cv, need)) return r;
-    c->cap_hub = need;
+  const long long maxd = c->ctr_h->max_degree;
+  if (maxd > c->tune.warp_slots / 2 && maxd > 32) {
+    // a class-6 vertex may overflow its shared table: 2 * warp_max slots per warp
+    const long long need = warp_grid_warps(c->tune, c->di) * 2ll * c->tune.warp_max;
+    if (int r = grow(c, c->wtab, c->cap_wtab, need)) return r;
+  }
+  if (maxd > c->tune.warp_max) {
+    const long long need = block_grid_size(c->tune, c->di) * 2ll * maxd;
+    if (int r = grow(c, c->btab, c->cap_btab, need)) return r;
   }
   return GSL_OK;
 }
 
-long long hub_region(gsl_ctx* c) { return 2 * c->ctr_h->max_degree; }
 
 int reset_sweep_counters(gsl_ctx* c, cudaStream_t s) {
   CK(cudaMemsetAsync(c->ctr, 0, offsetof(Counters, err), s));
@@ -257,9 +259,10 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
   a.w = weights;
   a.ctr = c->ctr;
   a.work = c->work;
-  a.hub_keys = c->hub_keys;
-  a.hub_vals = c->hub_vals;
-  a.hub_region = hub_region(c);
+  a.wtab = c->wtab;
+  a.wtab_region = 2ll * c->tune.warp_max;
+  a.btab = c->btab;
+  a.btab_region = 2ll * c->ctr_h->max_degree;
   a.n = n;
   int t = 0;
   bool converged = false, marked_prev = false;
@@ -284,6 +287,10 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     a.fnext = c->flag[(t + 1) & 1];
     a.ident = (!async_mode && !labels_init && t == 1) ? 1 : 0;
     a.check = t == 1 ? 1 : 0;
+    // the first sweep that gathers labels after the identity sweep sees
+    // almost as many distinct labels as neighbours (about 0.3 d on R-MAT
+    // hubs): hubs beyond three shared tables' worth go to global tables
+    a.gthresh = (t == 2 && !async_mode && !labels_init) ? 3 * c->tune.blk_slots : 0;
     // Sweep 1 changes every vertex that has a neighbour, and a sweep after
     // one that changed more than half of the vertices is run on all
     // vertices: marking would select nearly everything anyway.
@@ -492,7 +499,7 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   if (!c) return GSL_OK;
   DeviceGuard dg(c->device);
   void* dptrs[] = {c->lab[0], c->lab[1], c->flag[0], c->flag[1], c->work, c->parent, c->rank, c->sigma,
-                   c->block_sums, c->partials, c->hub_keys, c->hub_vals, c->ctr, c->sums, c->k_dev,
+                   c->block_sums, c->partials, c->wtab, c->btab, c->ctr, c->sums, c->k_dev,
                    c->st_off, c->st_col, c->st_w, c->st_lab};
   for (void* p : dptrs)
     if (p) cudaFree(p);
@@ -508,12 +515,8 @@ int gsl_ctx_destroy(gsl_ctx* c) {
 
 int gsl_ctx_set_tuning(gsl_ctx* c, int32_t warp_max, int32_t blk_max) {
   if (!c) return GSL_ERR_INVALID;
-  if (warp_max < 32 || warp_max > 1024 || blk_max < warp_max)
-    return fail(c, GSL_ERR_INVALID, "need 32 <= warp_max <= 1024 and blk_max >= warp_max");
-  const long long smem_blk = 2ll * 2 * blk_max * (long long)sizeof(unsigned) + 1024;
-  if (smem_blk > c->di.max_smem_optin)
-    return fail(c, GSL_ERR_INVALID, "blk_max %d needs %lld bytes of shared memory (max %d)", blk_max, smem_blk,
-                c->di.max_smem_optin);
+  if (warp_max < 32 || warp_max > (1 << 20) || blk_max < warp_max)
+    return fail(c, GSL_ERR_INVALID, "need 32 <= warp_max <= 2^20 and blk_max >= warp_max");
   c->tune.warp_max = warp_max;
   c->tune.blk_max = blk_max;
   return GSL_OK;

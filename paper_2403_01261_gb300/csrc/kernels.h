@@ -16,23 +16,25 @@ struct SweepArgs {
   unsigned char* fnext;      // frontier flags of the next sweep (set, never cleared here)
   const int* work;           // worklist (class regions at Counters::cls_start)
   Counters* ctr;
-  unsigned* hub_keys;        // global hash tables of the hub kernel, one region per block
-  unsigned* hub_vals;
-  long long hub_region;      // slots per block region
+  unsigned long long* wtab;  // global fallback tables of the warp kernel, one region per warp
+  long long wtab_region;     // slots per warp region (2 * warp_max)
+  unsigned long long* btab;  // global fallback tables of the block kernel, one region per block
+  long long btab_region;     // slots per block region (2 * largest degree of classes 7-8)
   long long n;
+  int gthresh;               // hub degree above which the block kernel goes straight to global tables (0: never)
   int ident;                 // prev is the identity labelling (not read)
   int check;                 // validate weights and weighted degrees
   int mark;                  // mark neighbours of changed vertices in fnext
 };
 
 struct Tuning {
-  int warp_max = 128;        // class 6 upper degree bound (one warp, smem table)
-  int blk_max = 4096;        // class 7 upper degree bound (one block, smem table)
+  int warp_max = 1024;       // class 6 upper degree bound (one warp per vertex)
+  int blk_max = 32768;       // class 7 upper degree bound (one block per vertex; above: class 8)
+  int warp_slots = 1024;     // shared-memory table slots per warp (8 bytes each)
+  int blk_slots = 12288;     // shared-memory table slots per block
   int group_block = 256;     // threads per block of the lane-group kernels
   int warp_block = 256;      // threads per block of the warp kernel
   int blk_block = 512;       // threads per block of the block kernel
-  int hub_block = 1024;      // threads per block of the hub kernel
-  int hub_grid = 0;          // blocks of the hub kernel (0: one per SM)
 };
 
 struct DeviceInfo {
@@ -53,7 +55,8 @@ void count_launches(long long k);   // process-wide tally of kernels this librar
 long long launches_total();
 cudaError_t launch_init_labels(const int* init, int* a, int* b, long long n, Counters* ctr,
                                const DeviceInfo& di, cudaStream_t s);
-long long hub_grid_size(const Tuning& t, const DeviceInfo& di);
+long long block_grid_size(const Tuning& t, const DeviceInfo& di);   // blocks of the class 7/8 kernel
+long long warp_grid_warps(const Tuning& t, const DeviceInfo& di);   // warps of the class 6 kernel
 
 // split_kernels.cu
 cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels,

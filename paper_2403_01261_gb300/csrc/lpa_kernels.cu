@@ -35,7 +35,6 @@ namespace gsl {
 
 namespace {
 
-constexpr unsigned EMPTY = 0xFFFFFFFFu;   // labels are < 2^31, never EMPTY
 constexpr int PROBE_CAP = 1 << 24;        // bound on open-addressing probes
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -100,25 +99,6 @@ __device__ __forceinline__ void flush_counters(Counters* ctr, int cls, unsigned 
       atomicAdd(&ctr->cls_scanned[cls], acc[1]);
     }
   }
-}
-
-// Open-addressing insert (linear probing, cap slots, any cap).  Returns the
-// label's new sum, or 0 if the probe bound was hit.
-template <bool GLOBAL>
-__device__ __forceinline__ unsigned table_add(unsigned* keys, unsigned* vals, unsigned cap, unsigned lbl,
-                                              unsigned c, int* err) {
-  unsigned h = __umulhi(hash32(lbl), cap);
-  for (int p = 0; p < PROBE_CAP; ++p) {
-    unsigned k = GLOBAL ? __ldcg(keys + h) : *(volatile unsigned*)(keys + h);
-    if (k == EMPTY) {
-      k = atomicCAS(keys + h, EMPTY, lbl);
-      if (k == EMPTY) k = lbl;
-    }
-    if (k == lbl) return atomicAdd(vals + h, c) + c;
-    if (++h == cap) h = 0;
-  }
-  raise_err(err, ERRBIT_TIMEOUT);
-  return 0;
 }
 
 // Loads entry e of a row: neighbour j (or -1 when e is past the row end or
@@ -352,44 +332,108 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 }
 
 // ---------------------------------------------------------------------------
-// Class 6: one warp per vertex, shared-memory table of `capw` slots per warp.
-template <bool WEIGHTED, bool ASYNC>
-__global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int capw) {
-  extern __shared__ unsigned smem_w[];
+// Hash tables of the d > 32 kernels.  A slot is 64 bits, (label << 32 | sum),
+// EMPTY64 when free.  A new label claims a slot with one atomicCAS; an
+// existing label adds its count with one atomicAdd on the whole word (sums
+// stay below 2^31, so the label half never changes).  Linear probing from
+// __umulhi(hash, cap), so any capacity works.
+constexpr unsigned long long EMPTY64 = ~0ull;
+
+template <bool GLOBAL>
+__device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned cap, unsigned lbl, unsigned c,
+                                             bool& created, int* err) {
+  unsigned h = __umulhi(hash32(lbl), cap);
+  const unsigned long long mine = ((unsigned long long)lbl << 32) | c;
+  for (int p = 0; p < PROBE_CAP; ++p) {
+    unsigned long long x = GLOBAL ? __ldcg(tab + h) : *(volatile unsigned long long*)(tab + h);
+    if (x == EMPTY64) {
+      x = atomicCAS(tab + h, EMPTY64, mine);
+      if (x == EMPTY64) {
+        created = true;
+        return c;
+      }
+    }
+    if ((unsigned)(x >> 32) == lbl) {
+      const unsigned long long old = atomicAdd(tab + h, (unsigned long long)c);
+      return (unsigned)old + c;
+    }
+    if (++h == cap) h = 0;
+  }
+  raise_err(err, ERRBIT_TIMEOUT);
+  return 0;
+}
+
+// One warp aggregates row [s, s+d) of vertex v into `tab` (cap slots).
+// Four 32-entry chunks are loaded (columns, then labels) before any is
+// hashed, so each lane keeps eight loads in flight.  Within a chunk equal
+// labels are merged with __match_any_sync and only the lowest lane of each
+// group inserts.  Returns true (warp-uniform) as soon as more than `limit`
+// distinct labels have been inserted: the table is then abandoned.
+template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
+__device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, long long s, int d, unsigned long long* tab,
+                                         unsigned cap, unsigned limit, unsigned long long& best,
+                                         unsigned long long& wsum) {
   const int lane = threadIdx.x & 31;
-  unsigned* keys = smem_w + (size_t)(threadIdx.x >> 5) * 2 * capw;
-  unsigned* vals = keys + capw;
-  const unsigned cnt = a.ctr->cls_count[CLS_WARP];
-  const int* __restrict__ work = a.work + a.ctr->cls_start[CLS_WARP];
+  for (unsigned k = lane; k < cap; k += 32) tab[k] = EMPTY64;
+  __syncwarp();
+  unsigned used = 0;
+  for (int e0 = 0; e0 < d; e0 += 128) {
+    int j[4], w[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, s, d, e0 + 32 * u + lane, j[u], w[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j[u] >= 0) wsum += (unsigned long long)w[u];
+      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u]) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned m = __match_any_sync(FULL, l[u]);
+      const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+      bool created = false;
+      if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+        const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+        const unsigned long long k = pack_key(sum, l[u]);
+        best = k > best ? k : best;
+      }
+      used += __popc(__ballot_sync(FULL, created));
+    }
+    if (used > limit) return true;   // at most 128 slots past the limit
+  }
+  return false;
+}
+
+// Class 6: one warp per vertex, `tw` slots of shared memory per warp.  A
+// vertex whose labels overflow the shared table is redone in the warp's
+// region of the global fallback tables (2 * warp_max slots).
+template <bool WEIGHTED, bool ASYNC>
+__global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int tw) {
+  extern __shared__ unsigned long long smem_w64[];
+  const int lane = threadIdx.x & 31;
+  unsigned long long* tab = smem_w64 + (size_t)(threadIdx.x >> 5) * tw;
   const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long* gtab = a.wtab + warp_id * a.wtab_region;
+  const unsigned cnt = a.ctr->cls_count[CLS_WARP];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[CLS_WARP];
   unsigned long long my_dn = 0, my_scan = 0;
   for (long long item = warp_id; item < (long long)cnt; item += nwarps) {
     const int v = work[item];
     const long long s = a.off[v];
     const int d = (int)(a.off[v + 1] - s);
     unsigned long long best = 0, wsum = 0;
-    bool sorted = false;
-    if (a.ident && !ASYNC) sorted = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, best, wsum));
-    if (!sorted) {
+    bool done = false;
+    if (a.ident && !ASYNC) done = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, best, wsum));
+    if (!done) {
       best = 0;
       wsum = 0;
-      const unsigned cap = (unsigned)(2 * d) < (unsigned)capw ? (unsigned)(2 * d) : (unsigned)capw;
-      for (unsigned k = lane; k < cap; k += 32) { keys[k] = EMPTY; vals[k] = 0; }
-      __syncwarp();
-      for (int e0 = 0; e0 < d; e0 += 32) {
-        int j, wt;
-        load_entry<WEIGHTED>(a, s, d, e0 + lane, j, wt);
-        const bool valid = j >= 0 && j != v;
-        if (j >= 0) wsum += (unsigned long long)wt;
-        const int lbl = valid ? gather_label<ASYNC>(a, j) : -1;
-        const unsigned m = __match_any_sync(FULL, lbl);
-        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)wt) : (unsigned)__popc(m);
-        if (valid && (m & lanemask_lt()) == 0) {
-          const unsigned sum = table_add<false>(keys, vals, cap, (unsigned)lbl, c, &a.ctr->err);
-          const unsigned long long k = pack_key(sum, lbl);
-          best = k > best ? k : best;
-        }
+      const unsigned want = 2u * (unsigned)d;
+      const unsigned cap = want < (unsigned)tw ? want : (unsigned)tw;
+      const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
+      if (warp_row<WEIGHTED, ASYNC, false>(a, v, s, d, tab, cap, limit, best, wsum)) {
+        best = 0;
+        wsum = 0;
+        warp_row<WEIGHTED, ASYNC, true>(a, v, s, d, gtab, want, 0xFFFFFFFFu, best, wsum);
       }
       __syncwarp();
     }
@@ -417,83 +461,113 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int capw) 
   flush_counters(a.ctr, CLS_WARP, my_dn, my_scan);
 }
 
-// ---------------------------------------------------------------------------
-// Classes 7 and 8: one block per vertex.  GLOBAL selects the table: shared
-// memory (class 7, `cap_slots` slots of dynamic shared memory) or the
-// block's own region of the global hub tables (class 8).
+// One block aggregates row [s, s+d) of v into `tab`; every warp takes
+// 128-entry chunks.  Before each chunk a warp checks the block's overflow
+// flag, and after it adds its new slots to the block's count; past `limit`
+// the flag is raised.  Returns the flag (block-uniform after the barrier).
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
-__global__ void __launch_bounds__(1024) sweep_block_kernel(SweepArgs a, int cls, unsigned cap_slots) {
-  extern __shared__ unsigned smem_b[];
-  __shared__ unsigned long long red[33];
-  __shared__ int s_changed;
-  __shared__ unsigned long long s_wtot;
-  unsigned* keys;
-  unsigned* vals;
-  if (GLOBAL) {
-    keys = a.hub_keys + (long long)blockIdx.x * a.hub_region;
-    vals = a.hub_vals + (long long)blockIdx.x * a.hub_region;
-  } else {
-    keys = smem_b;
-    vals = smem_b + cap_slots;
+__device__ __forceinline__ int block_row(const SweepArgs& a, int v, long long s, int d, unsigned long long* tab,
+                                         unsigned cap, unsigned limit, unsigned long long& best,
+                                         unsigned long long& wsum, unsigned* s_used, volatile int* s_ovf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
+  if (threadIdx.x == 0) {
+    *s_used = 0;
+    *s_ovf = 0;
   }
+  __syncthreads();
+  for (int e0 = wid * 128; e0 < d; e0 += nw * 128) {
+    int j[4], w[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, s, d, e0 + 32 * u + lane, j[u], w[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j[u] >= 0) wsum += (unsigned long long)w[u];
+      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u]) : -1;
+    }
+    bool stop = false;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!stop) {
+        const int f = __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0);
+        if (f) {
+          stop = true;
+        } else {
+          const unsigned m = __match_any_sync(FULL, l[u]);
+          const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+          bool created = false;
+          if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+            const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+            const unsigned long long k = pack_key(sum, l[u]);
+            best = k > best ? k : best;
+          }
+          const unsigned nc = __popc(__ballot_sync(FULL, created));
+          if (lane == 0 && nc && atomicAdd(s_used, nc) + nc > limit) *s_ovf = 1;
+        }
+      }
+    }
+    if (stop) break;
+  }
+  __syncthreads();
+  return *s_ovf;
+}
+
+// Classes 7 and 8: one block per vertex, `tb` slots of shared memory; a
+// vertex whose labels overflow it (or, when `gthresh` > 0, whose degree
+// exceeds gthresh) is aggregated in the block's region of the global
+// fallback tables instead (a.btab_region slots).
+template <bool WEIGHTED, bool ASYNC>
+__global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, unsigned tb, int gthresh) {
+  extern __shared__ unsigned long long smem_b64[];
+  __shared__ unsigned long long s_best, s_wsum;
+  __shared__ unsigned s_used;
+  __shared__ int s_ovf, s_changed;
+  unsigned long long* gtab = a.btab + (long long)blockIdx.x * a.btab_region;
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
   const int lane = threadIdx.x & 31;
-  const int nthreads = blockDim.x;
+  const unsigned nw = blockDim.x >> 5;
   unsigned long long my_dn = 0, my_scan = 0;
   for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
     const int v = work[item];
     const long long s = a.off[v];
     const int d = (int)(a.off[v + 1] - s);
     unsigned long long best = 0, wsum = 0;
+    if (threadIdx.x == 0) {
+      s_best = 0;
+      s_wsum = 0;
+    }
     int sorted = 0;
-    if (a.ident && !ASYNC) sorted = __syncthreads_and(ident_sorted_pass<WEIGHTED>(a, v, s, d, threadIdx.x, nthreads, best, wsum));
+    if (a.ident && !ASYNC)
+      sorted = __syncthreads_and(ident_sorted_pass<WEIGHTED>(a, v, s, d, threadIdx.x, blockDim.x, best, wsum));
     if (!sorted) {
       best = 0;
       wsum = 0;
-      const long long want = 2ll * d;
-      const unsigned cap = (unsigned)(want < (long long)cap_slots ? want : (long long)cap_slots);
-      for (unsigned k = threadIdx.x; k < cap; k += nthreads) { keys[k] = EMPTY; vals[k] = 0; }
-      __syncthreads();
-      // each warp takes 32-entry chunks; two chunks in flight per step
-      const int wid = threadIdx.x >> 5, nw = nthreads >> 5;
-      for (int e0 = wid * 64; e0 < d; e0 += nw * 64) {
-        int j0, w0, j1, w1;
-        load_entry<WEIGHTED>(a, s, d, e0 + lane, j0, w0);
-        load_entry<WEIGHTED>(a, s, d, e0 + 32 + lane, j1, w1);
-        const bool v0 = j0 >= 0 && j0 != v, v1 = j1 >= 0 && j1 != v;
-        if (j0 >= 0) wsum += (unsigned long long)w0;
-        if (j1 >= 0) wsum += (unsigned long long)w1;
-        const int l0 = v0 ? gather_label<ASYNC>(a, j0) : -1;
-        const int l1 = v1 ? gather_label<ASYNC>(a, j1) : -1;
-        const unsigned m0 = __match_any_sync(FULL, l0);
-        const unsigned c0 = WEIGHTED ? __reduce_add_sync(m0, (unsigned)w0) : (unsigned)__popc(m0);
-        if (v0 && (m0 & lanemask_lt()) == 0) {
-          const unsigned sum = table_add<GLOBAL>(keys, vals, cap, (unsigned)l0, c0, &a.ctr->err);
-          const unsigned long long k = pack_key(sum, l0);
-          best = k > best ? k : best;
-        }
-        const unsigned m1 = __match_any_sync(FULL, l1);
-        const unsigned c1 = WEIGHTED ? __reduce_add_sync(m1, (unsigned)w1) : (unsigned)__popc(m1);
-        if (v1 && (m1 & lanemask_lt()) == 0) {
-          const unsigned sum = table_add<GLOBAL>(keys, vals, cap, (unsigned)l1, c1, &a.ctr->err);
-          const unsigned long long k = pack_key(sum, l1);
-          best = k > best ? k : best;
-        }
+      const unsigned want = 2u * (unsigned)d;
+      int ovf = 1;
+      if (!(gthresh > 0 && d > gthresh) && want / 4 * 3 > 0) {
+        const unsigned cap = want < tb ? want : tb;
+        const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, s, d, smem_b64, cap, limit, best, wsum, &s_used, &s_ovf);
       }
+      if (ovf) {
+        best = 0;
+        wsum = 0;
+        block_row<WEIGHTED, ASYNC, true>(a, v, s, d, gtab, want, 0xFFFFFFFFu, best, wsum, &s_used, &s_ovf);
+      }
+      (void)nw;
     }
-    best = block_max_u64(best, red);
+    best = warp_max_u64(best);
+    if (lane == 0 && best) atomicMax(&s_best, best);
     if (WEIGHTED && a.check) {
       wsum = warp_sum_u64(wsum);
-      if (threadIdx.x == 0) s_wtot = 0;
-      __syncthreads();
-      if (lane == 0 && wsum) atomicAdd(&s_wtot, wsum);
-      __syncthreads();
-      if (threadIdx.x == 0 && s_wtot >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+      if (lane == 0 && wsum) atomicAdd(&s_wsum, wsum);
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
+      if (WEIGHTED && a.check && s_wsum >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
       const int old = own_label<ASYNC>(a, v);
-      const int nl = best ? (int)~(unsigned)best : old;
+      const int nl = s_best ? (int)~(unsigned)s_best : old;
       const bool changed = nl != old;
       store_label<ASYNC>(a, v, nl, changed);
       my_scan += (unsigned long long)d;
@@ -502,7 +576,7 @@ __global__ void __launch_bounds__(1024) sweep_block_kernel(SweepArgs a, int cls,
     }
     __syncthreads();
     if (s_changed && a.mark) {
-      for (int e = threadIdx.x; e < d; e += nthreads) {
+      for (int e = threadIdx.x; e < d; e += blockDim.x) {
         const int j = ld_stream(a.col + s + e);
         if ((unsigned)j < (unsigned)a.n) a.fnext[j] = 1;
       }
@@ -524,8 +598,6 @@ int occupancy_grid(K kernel, int block, size_t smem, const DeviceInfo& di) {
   return per_sm * di.sm_count;
 }
 
-int warp_cap(const Tuning& t) { return (int)next_pow2((unsigned)(2 * t.warp_max)); }
-int block_cap(const Tuning& t) { return 2 * t.blk_max; }
 
 template <bool W, bool A>
 cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
@@ -545,8 +617,8 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
     GSL_LAUNCH_GROUP(32, 5)
 #undef GSL_LAUNCH_GROUP
     case CLS_WARP: {
-      const int capw = warp_cap(t);
-      const size_t smem = (size_t)(t.warp_block / 32) * 2 * capw * sizeof(unsigned);
+      const int tw = t.warp_slots;
+      const size_t smem = (size_t)(t.warp_block / 32) * tw * sizeof(unsigned long long);
       static int grid = 0;
       static size_t grid_smem = 0;
       if (!grid || grid_smem != smem) {
@@ -554,25 +626,20 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
         grid = occupancy_grid(sweep_warp_kernel<W, A>, t.warp_block, smem, di);
         grid_smem = smem;
       }
-      sweep_warp_kernel<W, A><<<grid, t.warp_block, smem, s>>>(a, capw);
+      sweep_warp_kernel<W, A><<<grid, t.warp_block, smem, s>>>(a, tw);
       break;
     }
-    case CLS_BLOCK: {
-      const int capb = block_cap(t);
-      const size_t smem = (size_t)2 * capb * sizeof(unsigned);
-      static int grid = 0;
-      static size_t grid_smem = 0;
-      if (!grid || grid_smem != smem) {
-        cudaFuncSetAttribute(sweep_block_kernel<W, A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        grid = occupancy_grid(sweep_block_kernel<W, A, false>, t.blk_block, smem, di);
-        grid_smem = smem;
-      }
-      sweep_block_kernel<W, A, false><<<grid, t.blk_block, smem, s>>>(a, CLS_BLOCK, (unsigned)capb);
-      break;
-    }
+    case CLS_BLOCK:
     case CLS_HUB: {
-      const int grid = (int)hub_grid_size(t, di);
-      sweep_block_kernel<W, A, true><<<grid, t.hub_block, 0, s>>>(a, CLS_HUB, (unsigned)a.hub_region);
+      const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
+      static size_t attr_smem = 0;
+      if (attr_smem != smem) {
+        cudaFuncSetAttribute(sweep_block_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_smem = smem;
+      }
+      const int grid = (int)block_grid_size(t, di);
+      sweep_block_kernel<W, A><<<grid, t.blk_block, smem, s>>>(a, cls, (unsigned)t.blk_slots,
+                                                               cls == CLS_HUB ? a.gthresh : 0);
       break;
     }
     default:
@@ -589,7 +656,25 @@ std::atomic<long long> g_launches{0};
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
-long long hub_grid_size(const Tuning& t, const DeviceInfo& di) { return t.hub_grid > 0 ? t.hub_grid : di.sm_count; }
+long long block_grid_size(const Tuning& t, const DeviceInfo& di) {
+  int per_sm = 0;
+  const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
+  cudaFuncSetAttribute(sweep_block_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_block_kernel<false, false>, t.blk_block, smem);
+  cudaGetLastError();
+  if (per_sm < 1) per_sm = 1;
+  return (long long)per_sm * di.sm_count;
+}
+
+long long warp_grid_warps(const Tuning& t, const DeviceInfo& di) {
+  int per_sm = 0;
+  const size_t smem = (size_t)(t.warp_block / 32) * t.warp_slots * sizeof(unsigned long long);
+  cudaFuncSetAttribute(sweep_warp_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_warp_kernel<false, false>, t.warp_block, smem);
+  cudaGetLastError();
+  if (per_sm < 1) per_sm = 1;
+  return (long long)per_sm * di.sm_count * (t.warp_block / 32);
+}
 
 cudaError_t launch_class_histogram(const long long* off, long long n, long long nnz, const Tuning& t, Counters* ctr,
                                    const DeviceInfo& di, cudaStream_t s) {
