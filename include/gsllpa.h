@@ -146,6 +146,29 @@ int gsl_split(gsl_ctx* ctx, const gsl_csr* g, const int32_t* labels_in, int32_t*
 int gsl_modularity(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, const int32_t* labels,
                    double* q_out, void* stream);
 
+/* Modularity without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- a
+ * request loop that must not pay the device-wide synchronisation that
+ * cudaMalloc / cudaFree can cause, or a process whose GPU memory is already
+ * reserved in full by another allocator.  It needs no context and computes
+ * the same value as gsl_modularity (same exact integer sums, same double
+ * combine), with all scratch in one fixed device array that the library
+ * reserves on every GPU that loads it (about 32 MB, until the process
+ * exits).  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   g, weights, labels, q_out, stream   as for gsl_modularity; the graph is
+ *              on the current CUDA device.
+ *   n          at most GSL_NOALLOC_MAX_N vertices; larger graphs return
+ *              GSL_ERR_INVALID without touching the device.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array and clears what it needs at its start, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Returns GSL_ERR_INVALID for
+ * malformed input detected on the device, GSL_ERR_CUDA for a runtime error. */
+#define GSL_NOALLOC_MAX_N 4194304
+int gsl_modularity_noalloc(const gsl_csr* g, const int32_t* weights, const int32_t* labels,
+                           double* q_out, void* stream);
+
 /* GSL-LPA: lpa() of Algorithm 3 including its final split, i.e. gsl_lpa
  * from C = [0 .. n) followed by gsl_split with renumber = 0.  labels_out
  * receives connected-community labels (smallest vertex id of each piece). */
