@@ -14,14 +14,16 @@ constexpr int ERRBIT_TIMEOUT = 4;   // a bounded retry loop ran out
 
 // Degree classes of the sweep.  A vertex of degree d goes to
 //   class 0..5 : d in [1,1], [2,2], [3,4], [5,8], [9,16], [17,32]  (lane groups of 1..32)
-//   class 6    : 32 < d <= warp_max     (one warp, shared-memory hash table)
-//   class 7    : warp_max < d <= blk_max (one block, shared-memory hash table)
-//   class 8    : d > blk_max             (one block, global-memory hash table)
+//   class 6    : 32 < d <= warp_small   (one warp, small shared-memory table)
+//   class 7    : warp_small < d <= warp_max (one warp, large shared-memory table)
+//   class 8    : warp_max < d <= blk_max   (one block, shared-memory table)
+//   class 9    : d > blk_max               (one block, may use global tables)
 // Degree-0 vertices never change label and are not binned.
-constexpr int NCLASS = 9;
-constexpr int CLS_WARP = 6;
-constexpr int CLS_BLOCK = 7;
-constexpr int CLS_HUB = 8;
+constexpr int NCLASS = 10;
+constexpr int CLS_WARP_S = 6;
+constexpr int CLS_WARP_L = 7;
+constexpr int CLS_BLOCK = 8;
+constexpr int CLS_HUB = 9;
 
 // Device-resident counters.  The per-sweep fields come first so that one
 // memset of [0, offsetof(err)) resets them between sweeps.
@@ -37,23 +39,26 @@ struct Counters {
   unsigned long long cls_total[NCLASS];  // all vertices per class
   unsigned long long cls_start[NCLASS];  // start of each class's region in the worklist
   long long max_degree;
+  int giant;                    // split: root of the most frequent sampled piece
+  int pad2;
 };
 
 __device__ __forceinline__ void raise_err(int* err, int bit) {
   if ((__ldcg(err) & bit) == 0) atomicOr(err, bit);
 }
 
-__device__ __forceinline__ int degree_class(long long d, int warp_max, int blk_max) {
+__device__ __forceinline__ int degree_class(long long d, int warp_small, int warp_max, int blk_max) {
   if (d <= 0) return -1;
-  if (d <= 32) return 32 - __clz((int)(d - 1)) ;  // 1->0, 2->1, 3..4->2, 5..8->3, 9..16->4, 17..32->5
-  if (d <= warp_max) return CLS_WARP;
+  if (d <= 32) return 32 - __clz((int)(d - 1));  // 1->0, 2->1, 3..4->2, 5..8->3, 9..16->4, 17..32->5
+  if (d <= warp_small) return CLS_WARP_S;
+  if (d <= warp_max) return CLS_WARP_L;
   if (d <= blk_max) return CLS_BLOCK;
   return CLS_HUB;
 }
 
 // Streaming load for data read exactly once (CSR columns / weights): no L1
 // allocation and an L2 evict-first policy, so the stream does not push the
-// label array out of L2.
+// label array out of L2.  Kernels create the policies once and pass them.
 __device__ __forceinline__ unsigned long long policy_evict_first() {
   unsigned long long p;
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -64,18 +69,20 @@ __device__ __forceinline__ unsigned long long policy_evict_last() {
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ int ld_stream(const int* p) {
+__device__ __forceinline__ int ld_stream(const int* p, unsigned long long pol) {
   int v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy_evict_first()));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ int ld_stream(const int* p) { return ld_stream(p, policy_evict_first()); }
 // Gather of a label that stays constant for the whole kernel (Jacobi sweep):
 // read-only path, L2 evict-last policy.
-__device__ __forceinline__ int ld_label_ro(const int* p) {
+__device__ __forceinline__ int ld_label_ro(const int* p, unsigned long long pol) {
   int v;
-  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy_evict_last()));
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ int ld_label_ro(const int* p) { return ld_label_ro(p, policy_evict_last()); }
 // Gather of a label that other threads may be writing (in-place sweep):
 // coherent at L2.
 __device__ __forceinline__ int ld_label_rw(const int* p) { return __ldcg(p); }

@@ -166,8 +166,8 @@ enum Slot { SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + 
 const char* slot_name(int k) {
   static const char* names[SL_N] = {"classify", "init_labels", "bin_frontier", "sweep_deg1", "sweep_deg2",
                                     "sweep_deg3_4", "sweep_deg5_8", "sweep_deg9_16", "sweep_deg17_32",
-                                    "sweep_warp", "sweep_block", "sweep_hub", "split_unionfind",
-                                    "split_count_renumber", "modularity"};
+                                    "sweep_warp_small", "sweep_warp_large", "sweep_block", "sweep_hub",
+                                    "split_unionfind", "split_count_renumber", "modularity"};
   return names[k];
 }
 
@@ -361,7 +361,7 @@ int run_split(gsl_ctx* c, const gsl_csr* g, const int32_t* labels_in, int32_t* l
   c->profile.slot[SL_BIN].bytes += 20.0 * (double)n;
   pe = prof_begin(c, s);
   CK(launch_split(OFF(g), g->cols, n, labels_in, c->work, c->ctr, c->parent, labels_out, c->tune, c->di, s));
-  prof_end(c, pe, SL_SPLIT, s, 11);
+  prof_end(c, pe, SL_SPLIT, s, 15);
   // per vertex: parent init, own label, offsets, compress read and label
   // write; per entry: the column and, for the half with j < u, the label
   c->profile.slot[SL_SPLIT].vertices += n;
@@ -401,7 +401,7 @@ int run_modularity(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const i
   const int pe = prof_begin(c, s);
   CK(launch_modularity(OFF(g), g->cols, weights, n, labels, c->work, c->ctr, c->sigma, c->partials, np, c->sums,
                        c->tune, c->di, s));
-  prof_end(c, pe, SL_MOD, s, 12);
+  prof_end(c, pe, SL_MOD, s, 13);
   // per vertex: offsets, label, Sigma update (read+write) and square pass;
   // per entry: column, neighbour label and weight
   c->profile.slot[SL_MOD].vertices += n;

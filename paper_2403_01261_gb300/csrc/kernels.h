@@ -30,11 +30,18 @@ struct SweepArgs {
 struct Tuning {
   int warp_max = 1024;       // class 6 upper degree bound (one warp per vertex)
   int blk_max = 32768;       // class 7 upper degree bound (one block per vertex; above: class 8)
-  int warp_slots = 1024;     // shared-memory table slots per warp (8 bytes each)
+  int warp_slots = 1024;     // shared-memory table slots per warp of class 7 (8 bytes each)
   int blk_slots = 12288;     // shared-memory table slots per block
   int group_block = 256;     // threads per block of the lane-group kernels
   int warp_block = 256;      // threads per block of the warp kernel
   int blk_block = 512;       // threads per block of the block kernel
+};
+
+// Degree bounds of the classes (see common.cuh).
+struct ClassBounds {
+  int warp_small;
+  int warp_max;
+  int blk_max;
 };
 
 struct DeviceInfo {
@@ -55,8 +62,9 @@ void count_launches(long long k);   // process-wide tally of kernels this librar
 long long launches_total();
 cudaError_t launch_init_labels(const int* init, int* a, int* b, long long n, Counters* ctr,
                                const DeviceInfo& di, cudaStream_t s);
-long long block_grid_size(const Tuning& t, const DeviceInfo& di);   // blocks of the class 7/8 kernel
-long long warp_grid_warps(const Tuning& t, const DeviceInfo& di);   // warps of the class 6 kernel
+long long block_grid_size(const Tuning& t, const DeviceInfo& di);   // blocks of the class 8/9 kernel
+long long warp_grid_warps(const Tuning& t, const DeviceInfo& di);   // warps of the class 7 kernel
+ClassBounds class_bounds(const Tuning& t);
 
 // split_kernels.cu
 cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels,

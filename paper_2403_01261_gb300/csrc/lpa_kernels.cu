@@ -8,18 +8,19 @@
 // threads add: the synchronous sweep is deterministic.
 //
 // Work is split by degree class (binning pass below):
-//   d <= 32     lane groups of G = 1..32 lanes, one vertex per group; equal
-//               labels are found with __match_any_sync and summed with
-//               __popc / __reduce_add_sync; the argmax is two __reduce_max.
-//   d <= 128    one warp per vertex; per-warp open-addressing table in
-//               shared memory.
-//   d <= 4096   one block per vertex; block table in shared memory.
-//   larger      one block per vertex; table in a global-memory region owned
-//               by the block (L2 resident for all but the largest hubs).
+//   d <= 32          lane groups of G = 1..32 lanes, one vertex per group;
+//                    equal labels are found with __match_any_sync and summed
+//                    with __popc / __reduce_add_sync; the argmax is two
+//                    __reduce_max_sync.  No shared memory.
+//   d <= warp_small  one warp per vertex, 4 KB shared table (never overflows).
+//   d <= warp_max    one warp per vertex, 8 KB shared table, global spill.
+//   d <= blk_max     one block per vertex, 96 KB shared table, global spill.
+//   larger           one block per vertex, straight to global tables when
+//                    labels are known to be mostly distinct.
 // The hash kernels never scan their table: every insert returns the new sum
 // of its label, each thread keeps the largest packed key it has produced,
 // and the final sum of every label is produced by the thread that added
-// last, so the block maximum of those keys is the argmax.
+// last, so the maximum of those keys is the argmax.
 //
 // Pruning (lpaMove(): a processed vertex is re-marked when a neighbour
 // changes): a vertex whose label changes sets the next-frontier flag of each
@@ -36,6 +37,7 @@ namespace gsl {
 namespace {
 
 constexpr int PROBE_CAP = 1 << 24;        // bound on open-addressing probes
+constexpr unsigned long long EMPTY64 = ~0ull;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -62,23 +64,6 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
   return x;
 }
 
-// Block-wide maximum; every thread must call; returns the result to all.
-__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* red) {
-  x = warp_max_u64(x);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (lane == 0) red[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    unsigned long long y = lane < nw ? red[lane] : 0ull;
-    y = warp_max_u64(y);
-    if (lane == 0) red[32] = y;
-  }
-  __syncthreads();
-  const unsigned long long r = red[32];
-  __syncthreads();
-  return r;
-}
-
 // Adds the per-thread sweep statistics of the whole block to the counters.
 __device__ __forceinline__ void flush_counters(Counters* ctr, int cls, unsigned long long dn,
                                                unsigned long long scanned) {
@@ -101,19 +86,24 @@ __device__ __forceinline__ void flush_counters(Counters* ctr, int cls, unsigned 
   }
 }
 
-// Loads entry e of a row: neighbour j (or -1 when e is past the row end or
-// j is out of range) and its weight.
+// Cache policies, created once per thread: columns and weights are streamed
+// (evict first), labels are gathered repeatedly (evict last).
+struct Pol {
+  unsigned long long stream, label;
+};
+__device__ __forceinline__ Pol make_pol() { return {policy_evict_first(), policy_evict_last()}; }
+
+// Entry e of the row starting at cp / wp: neighbour j (-1 past the row end
+// or when out of range) and its weight.
 template <bool WEIGHTED>
-__device__ __forceinline__ void load_entry(const SweepArgs& a, long long s, int d, int e, int& j, int& wt) {
+__device__ __forceinline__ void load_entry(const SweepArgs& a, const int* cp, const int* wp, int d, int e,
+                                           const Pol& pol, int& j, int& wt) {
   j = -1;
   wt = 0;
   if (e < d) {
-    j = ld_stream(a.col + s + e);
-    wt = WEIGHTED ? ld_stream(a.w + s + e) : 1;
-    if ((unsigned)j >= (unsigned)a.n) {
-      raise_err(&a.ctr->err, ERRBIT_INVALID);
-      j = -1;
-    } else if (WEIGHTED && a.check && wt <= 0) {
+    j = ld_stream(cp + e, pol.stream);
+    wt = WEIGHTED ? ld_stream(wp + e, pol.stream) : 1;
+    if ((unsigned)j >= (unsigned)a.n || (WEIGHTED && a.check && wt <= 0)) {
       raise_err(&a.ctr->err, ERRBIT_INVALID);
       j = -1;
     }
@@ -121,9 +111,9 @@ __device__ __forceinline__ void load_entry(const SweepArgs& a, long long s, int 
 }
 
 template <bool ASYNC>
-__device__ __forceinline__ int gather_label(const SweepArgs& a, int j) {
+__device__ __forceinline__ int gather_label(const SweepArgs& a, int j, const Pol& pol) {
   if (a.ident) return j;
-  return ASYNC ? ld_label_rw(a.prev + j) : ld_label_ro(a.prev + j);
+  return ASYNC ? ld_label_rw(a.prev + j) : ld_label_ro(a.prev + j, pol.label);
 }
 
 template <bool ASYNC>
@@ -143,8 +133,8 @@ __device__ __forceinline__ void store_label(const SweepArgs& a, int v, int nl, b
 // ---------------------------------------------------------------------------
 // Static classification of all vertices: class totals, region starts, max
 // degree; validates the offsets array.
-__global__ void class_histogram_kernel(const long long* __restrict__ off, long long n, long long nnz, int warp_max,
-                                       int blk_max, Counters* ctr) {
+__global__ void class_histogram_kernel(const long long* __restrict__ off, long long n, long long nnz, ClassBounds cb,
+                                       Counters* ctr) {
   __shared__ unsigned long long hist[NCLASS];
   __shared__ long long maxd;
   __shared__ int bad;
@@ -159,7 +149,7 @@ __global__ void class_histogram_kernel(const long long* __restrict__ off, long l
     const long long d = e - s;
     if (d >= (1ll << 31)) { lbad |= ERRBIT_OVERFLOW; continue; }
     lmax = d > lmax ? d : lmax;
-    const int c = degree_class(d, warp_max, blk_max);
+    const int c = degree_class(d, cb.warp_small, cb.warp_max, cb.blk_max);
     if (c >= 0) atomicAdd(&hist[c], 1ull);
     if (v == 0 && s != 0) lbad |= ERRBIT_INVALID;
     if (v == n - 1 && e != nnz) lbad |= ERRBIT_INVALID;
@@ -189,8 +179,8 @@ __global__ void class_starts_kernel(Counters* ctr) {
 constexpr int BIN_ITEMS = 8;
 
 __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ off, long long n,
-                                                   unsigned char* __restrict__ fcur, int all_active, int warp_max,
-                                                   int blk_max, int* __restrict__ work, Counters* ctr) {
+                                                   unsigned char* __restrict__ fcur, int all_active, ClassBounds cb,
+                                                   int* __restrict__ work, Counters* ctr) {
   __shared__ unsigned cnt[NCLASS];
   __shared__ unsigned base[NCLASS];
   const long long tile = (long long)blockDim.x * BIN_ITEMS;
@@ -206,7 +196,7 @@ __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ 
       if (v < n) {
         bool act = all_active != 0;
         if (!act && fcur[v]) { act = true; fcur[v] = 0; }
-        if (act) cls[k] = degree_class(off[v + 1] - off[v], warp_max, blk_max);
+        if (act) cls[k] = degree_class(off[v + 1] - off[v], cb.warp_small, cb.warp_max, cb.blk_max);
       }
       if (cls[k] >= 0) pos[k] = atomicAdd(&cnt[cls[k]], 1u);
     }
@@ -246,6 +236,7 @@ template <int G, bool WEIGHTED, bool ASYNC>
 __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) {
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const Pol pol = make_pol();
   const int lane = threadIdx.x & 31;
   const int gl = lane & (G - 1);
   const int gbase = lane & ~(G - 1);
@@ -266,10 +257,11 @@ __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) 
       d = (int)(a.off[v + 1] - s);
     }
     int j, wt;
-    load_entry<WEIGHTED>(a, s, d, gl, j, wt);
+    load_entry<WEIGHTED>(a, a.col + s, a.w + s, d, gl, pol, j, wt);
     const bool nb = j >= 0;
     const bool valid = nb && j != v;       // scanCommunities skips j == i
-    const int lbl = valid ? gather_label<ASYNC>(a, j) : -1;
+    const int lbl = valid ? gather_label<ASYNC>(a, j, pol) : -1;
+    const int old = (has && gl == 0) ? own_label<ASYNC>(a, v) : 0;
     if (WEIGHTED && a.check) {
       unsigned long long ws = nb ? (unsigned long long)wt : 0ull;
 #pragma unroll
@@ -284,7 +276,6 @@ __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) 
     const unsigned binv = __reduce_max_sync(gmask, cand);
     bool changed = false;
     if (has && gl == 0) {
-      const int old = own_label<ASYNC>(a, v);
       const int nl = mc ? (int)~binv : old;
       changed = nl != old;
       store_label<ASYNC>(a, v, nl, changed);
@@ -310,14 +301,16 @@ __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) 
 // `best` is the per-thread partial key; `wsum` the per-thread weight sum.
 template <bool WEIGHTED>
 __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, long long s, int d, int tid, int nthreads,
-                                                  unsigned long long& best, unsigned long long& wsum) {
+                                                  const Pol& pol, unsigned long long& best, unsigned long long& wsum) {
   bool sorted = true;
+  const int* cp = a.col + s;
+  const int* wp = a.w + s;
+  const int lane = tid & 31;
   for (int e0 = (tid & ~31); e0 < d; e0 += (nthreads & ~31)) {
-    const int lane = tid & 31;
     int j, wt;
-    load_entry<WEIGHTED>(a, s, d, e0 + lane, j, wt);
+    load_entry<WEIGHTED>(a, cp, wp, d, e0 + lane, pol, j, wt);
     int nxt = __shfl_down_sync(FULL, j, 1);
-    if (lane == 31 && e0 + 32 < d) nxt = ld_stream(a.col + s + e0 + 32);
+    if (lane == 31 && e0 + 32 < d) nxt = ld_stream(cp + e0 + 32, pol.stream);
     if (j >= 0 && e0 + lane + 1 < d && !(j < nxt)) sorted = false;
     if (j < 0 && e0 + lane < d) sorted = false;      // invalid entry: let the hash path handle it
     if (j >= 0) {
@@ -337,8 +330,6 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 // existing label adds its count with one atomicAdd on the whole word (sums
 // stay below 2^31, so the label half never changes).  Linear probing from
 // __umulhi(hash, cap), so any capacity works.
-constexpr unsigned long long EMPTY64 = ~0ull;
-
 template <bool GLOBAL>
 __device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned cap, unsigned lbl, unsigned c,
                                              bool& created, int* err) {
@@ -363,16 +354,16 @@ __device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned c
   return 0;
 }
 
-// One warp aggregates row [s, s+d) of vertex v into `tab` (cap slots).
-// Four 32-entry chunks are loaded (columns, then labels) before any is
-// hashed, so each lane keeps eight loads in flight.  Within a chunk equal
+// One warp aggregates the row (cp, wp, d) of vertex v into `tab` (cap
+// slots).  Four 32-entry chunks are loaded (columns, then labels) before any
+// is hashed, so each lane keeps eight loads in flight.  Within a chunk equal
 // labels are merged with __match_any_sync and only the lowest lane of each
-// group inserts.  Returns true (warp-uniform) as soon as more than `limit`
+// group inserts.  Returns true (warp-uniform) once more than `limit`
 // distinct labels have been inserted: the table is then abandoned.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
-__device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, long long s, int d, unsigned long long* tab,
-                                         unsigned cap, unsigned limit, unsigned long long& best,
-                                         unsigned long long& wsum) {
+__device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
+                                         unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
+                                         unsigned long long& best, unsigned long long& wsum) {
   const int lane = threadIdx.x & 31;
   for (unsigned k = lane; k < cap; k += 32) tab[k] = EMPTY64;
   __syncwarp();
@@ -380,60 +371,82 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, long long s,
   for (int e0 = 0; e0 < d; e0 += 128) {
     int j[4], w[4], l[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, s, d, e0 + 32 * u + lane, j[u], w[u]);
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (j[u] >= 0) wsum += (unsigned long long)w[u];
-      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u]) : -1;
+      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const unsigned m = __match_any_sync(FULL, l[u]);
-      const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
-      bool created = false;
-      if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
-        const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
-        const unsigned long long k = pack_key(sum, l[u]);
-        best = k > best ? k : best;
+      if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
+        const unsigned m = __match_any_sync(FULL, l[u]);
+        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+        bool created = false;
+        if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+          const unsigned long long k = pack_key(sum, l[u]);
+          best = k > best ? k : best;
+        }
+        if (limit != 0xFFFFFFFFu) used += __popc(__ballot_sync(FULL, created));
       }
-      used += __popc(__ballot_sync(FULL, created));
     }
     if (used > limit) return true;   // at most 128 slots past the limit
   }
   return false;
 }
 
-// Class 6: one warp per vertex, `tw` slots of shared memory per warp.  A
-// vertex whose labels overflow the shared table is redone in the warp's
-// region of the global fallback tables (2 * warp_max slots).
-template <bool WEIGHTED, bool ASYNC>
-__global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int tw) {
+// Classes 6 and 7: one warp per vertex, TW slots of shared memory per warp.
+// With SPILL, a vertex whose labels overflow the shared table is redone in
+// the warp's region of the global fallback tables (2 * warp_max slots);
+// without it the class bound guarantees 2 d <= TW.  The next vertex's
+// worklist entry and offsets are loaded while the current one is processed.
+template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL>
+__global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
   extern __shared__ unsigned long long smem_w64[];
   const int lane = threadIdx.x & 31;
-  unsigned long long* tab = smem_w64 + (size_t)(threadIdx.x >> 5) * tw;
+  unsigned long long* tab = smem_w64 + (size_t)(threadIdx.x >> 5) * TW;
   const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  unsigned long long* gtab = a.wtab + warp_id * a.wtab_region;
-  const unsigned cnt = a.ctr->cls_count[CLS_WARP];
-  const int* __restrict__ work = a.work + a.ctr->cls_start[CLS_WARP];
+  unsigned long long* gtab = SPILL ? a.wtab + warp_id * a.wtab_region : nullptr;
+  const unsigned cnt = a.ctr->cls_count[cls];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const Pol pol = make_pol();
   unsigned long long my_dn = 0, my_scan = 0;
-  for (long long item = warp_id; item < (long long)cnt; item += nwarps) {
-    const int v = work[item];
-    const long long s = a.off[v];
-    const int d = (int)(a.off[v + 1] - s);
+  long long item = warp_id;
+  int vn = 0;
+  long long sn = 0, en = 0;
+  if (item < (long long)cnt) {
+    vn = work[item];
+    sn = a.off[vn];
+    en = a.off[vn + 1];
+  }
+  while (item < (long long)cnt) {
+    const int v = vn;
+    const long long s = sn;
+    const int d = (int)(en - sn);
+    const long long next_item = item + nwarps;
+    if (next_item < (long long)cnt) {
+      vn = work[next_item];
+      sn = a.off[vn];
+      en = a.off[vn + 1];
+    }
+    const int old = own_label<ASYNC>(a, v);
+    const int* cp = a.col + s;
+    const int* wp = a.w + s;
     unsigned long long best = 0, wsum = 0;
     bool done = false;
-    if (a.ident && !ASYNC) done = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, best, wsum));
+    if (a.ident && !ASYNC) done = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, pol, best, wsum));
     if (!done) {
       best = 0;
       wsum = 0;
       const unsigned want = 2u * (unsigned)d;
-      const unsigned cap = want < (unsigned)tw ? want : (unsigned)tw;
-      const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
-      if (warp_row<WEIGHTED, ASYNC, false>(a, v, s, d, tab, cap, limit, best, wsum)) {
+      const unsigned cap = want < (unsigned)TW ? want : (unsigned)TW;
+      const unsigned limit = (!SPILL || cap >= want) ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
+      if (warp_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, tab, cap, limit, pol, best, wsum) && SPILL) {
         best = 0;
         wsum = 0;
-        warp_row<WEIGHTED, ASYNC, true>(a, v, s, d, gtab, want, 0xFFFFFFFFu, best, wsum);
+        warp_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum);
       }
       __syncwarp();
     }
@@ -442,7 +455,6 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int tw) {
       wsum = warp_sum_u64(wsum);
       if (lane == 0 && wsum >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
     }
-    const int old = own_label<ASYNC>(a, v);
     const int nl = best ? (int)~(unsigned)best : old;
     const bool changed = nl != old;
     if (lane == 0) {
@@ -452,23 +464,25 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int tw) {
     }
     if (changed && a.mark) {
       for (int e = lane; e < d; e += 32) {
-        const int j = ld_stream(a.col + s + e);
+        const int j = ld_stream(cp + e, pol.stream);
         if ((unsigned)j < (unsigned)a.n) a.fnext[j] = 1;
       }
       if (!ASYNC && lane == 0) a.fnext[v] = 1;
     }
+    item = next_item;
   }
-  flush_counters(a.ctr, CLS_WARP, my_dn, my_scan);
+  flush_counters(a.ctr, cls, my_dn, my_scan);
 }
 
-// One block aggregates row [s, s+d) of v into `tab`; every warp takes
-// 128-entry chunks.  Before each chunk a warp checks the block's overflow
-// flag, and after it adds its new slots to the block's count; past `limit`
-// the flag is raised.  Returns the flag (block-uniform after the barrier).
+// One block aggregates the row of v into `tab`; every warp takes 128-entry
+// chunks.  Before each chunk a warp checks the block's overflow flag, and
+// after it adds its new slots to the block's count; past `limit` the flag
+// is raised.  Returns the flag (block-uniform after the barrier).
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
-__device__ __forceinline__ int block_row(const SweepArgs& a, int v, long long s, int d, unsigned long long* tab,
-                                         unsigned cap, unsigned limit, unsigned long long& best,
-                                         unsigned long long& wsum, unsigned* s_used, volatile int* s_ovf) {
+__device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
+                                         unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
+                                         unsigned long long& best, unsigned long long& wsum, unsigned* s_used,
+                                         volatile int* s_ovf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
   if (threadIdx.x == 0) {
@@ -479,18 +493,17 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, long long s,
   for (int e0 = wid * 128; e0 < d; e0 += nw * 128) {
     int j[4], w[4], l[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, s, d, e0 + 32 * u + lane, j[u], w[u]);
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (j[u] >= 0) wsum += (unsigned long long)w[u];
-      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u]) : -1;
+      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
     }
     bool stop = false;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (!stop) {
-        const int f = __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0);
-        if (f) {
+      if (!stop && e0 + 32 * u < d) {
+        if (limit != 0xFFFFFFFFu && __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0)) {
           stop = true;
         } else {
           const unsigned m = __match_any_sync(FULL, l[u]);
@@ -501,8 +514,10 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, long long s,
             const unsigned long long k = pack_key(sum, l[u]);
             best = k > best ? k : best;
           }
-          const unsigned nc = __popc(__ballot_sync(FULL, created));
-          if (lane == 0 && nc && atomicAdd(s_used, nc) + nc > limit) *s_ovf = 1;
+          if (limit != 0xFFFFFFFFu) {
+            const unsigned nc = __popc(__ballot_sync(FULL, created));
+            if (lane == 0 && nc && atomicAdd(s_used, nc) + nc > limit) *s_ovf = 1;
+          }
         }
       }
     }
@@ -512,8 +527,8 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, long long s,
   return *s_ovf;
 }
 
-// Classes 7 and 8: one block per vertex, `tb` slots of shared memory; a
-// vertex whose labels overflow it (or, when `gthresh` > 0, whose degree
+// Classes 8 and 9: one block per vertex, `tb` slots of shared memory; a
+// vertex whose labels overflow it (or, when gthresh > 0, whose degree
 // exceeds gthresh) is aggregated in the block's region of the global
 // fallback tables instead (a.btab_region slots).
 template <bool WEIGHTED, bool ASYNC>
@@ -525,13 +540,15 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
   unsigned long long* gtab = a.btab + (long long)blockIdx.x * a.btab_region;
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const Pol pol = make_pol();
   const int lane = threadIdx.x & 31;
-  const unsigned nw = blockDim.x >> 5;
   unsigned long long my_dn = 0, my_scan = 0;
   for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
     const int v = work[item];
     const long long s = a.off[v];
     const int d = (int)(a.off[v + 1] - s);
+    const int* cp = a.col + s;
+    const int* wp = a.w + s;
     unsigned long long best = 0, wsum = 0;
     if (threadIdx.x == 0) {
       s_best = 0;
@@ -539,23 +556,23 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
     }
     int sorted = 0;
     if (a.ident && !ASYNC)
-      sorted = __syncthreads_and(ident_sorted_pass<WEIGHTED>(a, v, s, d, threadIdx.x, blockDim.x, best, wsum));
+      sorted = __syncthreads_and(ident_sorted_pass<WEIGHTED>(a, v, s, d, threadIdx.x, blockDim.x, pol, best, wsum));
     if (!sorted) {
       best = 0;
       wsum = 0;
       const unsigned want = 2u * (unsigned)d;
       int ovf = 1;
-      if (!(gthresh > 0 && d > gthresh) && want / 4 * 3 > 0) {
+      if (!(gthresh > 0 && d > gthresh)) {
         const unsigned cap = want < tb ? want : tb;
         const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, s, d, smem_b64, cap, limit, best, wsum, &s_used, &s_ovf);
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, smem_b64, cap, limit, pol, best, wsum, &s_used,
+                                                &s_ovf);
       }
       if (ovf) {
         best = 0;
         wsum = 0;
-        block_row<WEIGHTED, ASYNC, true>(a, v, s, d, gtab, want, 0xFFFFFFFFu, best, wsum, &s_used, &s_ovf);
+        block_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, &s_used, &s_ovf);
       }
-      (void)nw;
     }
     best = warp_max_u64(best);
     if (lane == 0 && best) atomicMax(&s_best, best);
@@ -577,7 +594,7 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
     __syncthreads();
     if (s_changed && a.mark) {
       for (int e = threadIdx.x; e < d; e += blockDim.x) {
-        const int j = ld_stream(a.col + s + e);
+        const int j = ld_stream(cp + e, pol.stream);
         if ((unsigned)j < (unsigned)a.n) a.fnext[j] = 1;
       }
       if (!ASYNC && threadIdx.x == 0) a.fnext[v] = 1;
@@ -590,14 +607,19 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
 // ---------------------------------------------------------------------------
 // launchers
 namespace {
+std::atomic<long long> g_launches{0};
+
 template <typename K>
 int occupancy_grid(K kernel, int block, size_t smem, const DeviceInfo& di) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+  cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
   return per_sm * di.sm_count;
 }
 
+constexpr int TW_SMALL = 512;    // slots per warp, class 6 (2 d <= 512)
+constexpr int TW_LARGE = 1024;   // slots per warp, class 7
 
 template <bool W, bool A>
 cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
@@ -616,17 +638,26 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
     GSL_LAUNCH_GROUP(16, 4)
     GSL_LAUNCH_GROUP(32, 5)
 #undef GSL_LAUNCH_GROUP
-    case CLS_WARP: {
-      const int tw = t.warp_slots;
-      const size_t smem = (size_t)(t.warp_block / 32) * tw * sizeof(unsigned long long);
+    case CLS_WARP_S: {
+      const size_t smem = (size_t)(t.warp_block / 32) * TW_SMALL * sizeof(unsigned long long);
       static int grid = 0;
-      static size_t grid_smem = 0;
-      if (!grid || grid_smem != smem) {
-        cudaFuncSetAttribute(sweep_warp_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        grid = occupancy_grid(sweep_warp_kernel<W, A>, t.warp_block, smem, di);
-        grid_smem = smem;
+      if (!grid) {
+        cudaFuncSetAttribute(sweep_warp_kernel<W, A, TW_SMALL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        grid = occupancy_grid(sweep_warp_kernel<W, A, TW_SMALL, false>, t.warp_block, smem, di);
       }
-      sweep_warp_kernel<W, A><<<grid, t.warp_block, smem, s>>>(a, tw);
+      sweep_warp_kernel<W, A, TW_SMALL, false><<<grid, t.warp_block, smem, s>>>(a, CLS_WARP_S);
+      break;
+    }
+    case CLS_WARP_L: {
+      const size_t smem = (size_t)(t.warp_block / 32) * TW_LARGE * sizeof(unsigned long long);
+      static int grid = 0;
+      if (!grid) {
+        cudaFuncSetAttribute(sweep_warp_kernel<W, A, TW_LARGE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        grid = occupancy_grid(sweep_warp_kernel<W, A, TW_LARGE, true>, t.warp_block, smem, di);
+      }
+      sweep_warp_kernel<W, A, TW_LARGE, true><<<grid, t.warp_block, smem, s>>>(a, CLS_WARP_L);
       break;
     }
     case CLS_BLOCK:
@@ -650,30 +681,43 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
 }
 }  // namespace
 
-namespace {
-std::atomic<long long> g_launches{0};
-}
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 long long block_grid_size(const Tuning& t, const DeviceInfo& di) {
+  static long long cached = 0;
+  static int cached_slots = 0, cached_block = 0;
+  if (cached && cached_slots == t.blk_slots && cached_block == t.blk_block) return cached;
   int per_sm = 0;
   const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
   cudaFuncSetAttribute(sweep_block_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_block_kernel<false, false>, t.blk_block, smem);
   cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
-  return (long long)per_sm * di.sm_count;
+  cached = (long long)per_sm * di.sm_count;
+  cached_slots = t.blk_slots;
+  cached_block = t.blk_block;
+  return cached;
 }
 
 long long warp_grid_warps(const Tuning& t, const DeviceInfo& di) {
   int per_sm = 0;
-  const size_t smem = (size_t)(t.warp_block / 32) * t.warp_slots * sizeof(unsigned long long);
-  cudaFuncSetAttribute(sweep_warp_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_warp_kernel<false, false>, t.warp_block, smem);
+  const size_t smem = (size_t)(t.warp_block / 32) * TW_LARGE * sizeof(unsigned long long);
+  cudaFuncSetAttribute(sweep_warp_kernel<false, false, TW_LARGE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_warp_kernel<false, false, TW_LARGE, true>,
+                                                t.warp_block, smem);
   cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
   return (long long)per_sm * di.sm_count * (t.warp_block / 32);
+}
+
+ClassBounds class_bounds(const Tuning& t) {
+  ClassBounds cb;
+  cb.warp_max = t.warp_max;
+  cb.warp_small = TW_SMALL / 2 < t.warp_max ? TW_SMALL / 2 : t.warp_max;
+  cb.blk_max = t.blk_max;
+  return cb;
 }
 
 cudaError_t launch_class_histogram(const long long* off, long long n, long long nnz, const Tuning& t, Counters* ctr,
@@ -681,7 +725,7 @@ cudaError_t launch_class_histogram(const long long* off, long long n, long long 
   if (n > 0) {
     long long blocks = (n + 255) / 256;
     const long long cap = 8ll * di.sm_count;
-    class_histogram_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, nnz, t.warp_max, t.blk_max, ctr);
+    class_histogram_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, nnz, class_bounds(t), ctr);
   }
   class_starts_kernel<<<1, 1, 0, s>>>(ctr);
   count_launches(n > 0 ? 2 : 1);
@@ -694,8 +738,7 @@ cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, i
   const long long tile = 256ll * BIN_ITEMS;
   long long blocks = (n + tile - 1) / tile;
   const long long cap = 8ll * di.sm_count;
-  bin_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, fcur, all_active, t.warp_max, t.blk_max, work,
-                                                                 ctr);
+  bin_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr);
   count_launches(1);
   return cudaGetLastError();
 }

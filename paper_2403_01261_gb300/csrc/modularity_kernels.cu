@@ -173,7 +173,8 @@ cudaError_t launch_modularity(const long long* off, const int* col, const int* w
     mod_group_kernel<8, true><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, 3, sigma, out);
     mod_group_kernel<16, true><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, 4, sigma, out);
     mod_group_kernel<32, true><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, 5, sigma, out);
-    mod_group_kernel<32, true><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_WARP, sigma, out);
+    mod_group_kernel<32, true><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_WARP_S, sigma, out);
+    mod_group_kernel<32, true><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_WARP_L, sigma, out);
     mod_block_kernel<true><<<4 * di.sm_count, 512, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_BLOCK, sigma, out);
     mod_block_kernel<true><<<4 * di.sm_count, 512, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_HUB, sigma, out);
   } else {
@@ -183,14 +184,15 @@ cudaError_t launch_modularity(const long long* off, const int* col, const int* w
     mod_group_kernel<8, false><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, 3, sigma, out);
     mod_group_kernel<16, false><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, 4, sigma, out);
     mod_group_kernel<32, false><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, 5, sigma, out);
-    mod_group_kernel<32, false><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_WARP, sigma, out);
+    mod_group_kernel<32, false><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_WARP_S, sigma, out);
+    mod_group_kernel<32, false><<<g, 256, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_WARP_L, sigma, out);
     mod_block_kernel<false><<<4 * di.sm_count, 512, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_BLOCK, sigma, out);
     mod_block_kernel<false><<<4 * di.sm_count, 512, 0, s>>>(off, col, w, labels, n, work, ctr, CLS_HUB, sigma, out);
   }
   const long long np = nparts < modularity_partials(di) ? nparts : modularity_partials(di);
   mod_square_kernel<<<(int)np, 256, 0, s>>>(sigma, n, partials);
   mod_final_kernel<<<1, 32, 0, s>>>(partials, np, out);
-  count_launches(12);
+  count_launches(13);
   return cudaGetLastError();
 }
 

@@ -7,10 +7,18 @@
 // C[u] == C[j], by lock-free union-find instead of one BFS per piece:
 //   - parent[v] <= v at all times; a union links the larger of two roots
 //     below the smaller with atomicCAS, so the root of every tree is the
-//     smallest vertex of its component;
+//     smallest vertex of its component -- Algorithm 2's label;
 //   - find follows parents with path halving (benign racy stores: every
 //     value written is an ancestor of the vertex);
-//   - each undirected edge is offered once, from its larger endpoint.
+//   - edges are offered in two phases (neighbour sampling after Sutton,
+//     Ben-Nun and Bar-Noy, "Optimizing Parallel Graph Connectivity
+//     Computation via Subgraph Sampling", IPDPS 2018): first every vertex
+//     links with its first SPLIT_SAMPLE row entries of its own community;
+//     after flattening, the most frequent root among sampled vertices names
+//     the largest piece, and only vertices outside it offer their remaining
+//     entries.  An edge between two vertices of that piece is redundant, and
+//     an edge leaving it is offered from its other end, so the components
+//     are the same as offering every edge.
 // All loops are bounded (parents strictly decrease along a path and a
 // failed CAS strictly lowers the root being linked); the bound is a safety
 // net that raises ERRBIT_TIMEOUT.
@@ -48,8 +56,9 @@ __device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err) {
   raise_err(err, ERRBIT_TIMEOUT);
 }
 
-// Offers the intra-community edges (u, j), j < u, of one row slice to the
-// union-find.
+constexpr int SPLIT_SAMPLE = 2;   // row entries linked per vertex before the largest piece is known
+
+// Offers entry e of u's row to the union-find if it is an intra-community edge.
 __device__ __forceinline__ void hook_entry(const int* col, const int* labels, int* p, long long n, int u, int cu,
                                            long long e, int* err) {
   const int j = ld_stream(col + e);
@@ -57,7 +66,7 @@ __device__ __forceinline__ void hook_entry(const int* col, const int* labels, in
     raise_err(err, ERRBIT_INVALID);
     return;
   }
-  if (j < u && ld_label_ro(labels + j) == cu) uf_unite(p, u, j, err);
+  if (j != u && ld_label_ro(labels + j) == cu) uf_unite(p, u, j, err);
 }
 
 }  // namespace
@@ -67,41 +76,99 @@ __global__ void init_parent_kernel(int* __restrict__ p, long long n) {
     p[v] = (int)v;
 }
 
-// Classes 0..6: G lanes per vertex, looping over the row in strides of G.
+// Phase 1: every vertex links with its first SPLIT_SAMPLE row entries.
+__global__ void sample_link_kernel(const long long* __restrict__ off, const int* __restrict__ col,
+                                   const int* __restrict__ labels, int* p, long long n, Counters* ctr) {
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+    const long long s = off[u], e = off[u + 1];
+    const int cu = labels[u];
+    for (int k = 0; k < SPLIT_SAMPLE && s + k < e; ++k) hook_entry(col, labels, p, n, (int)u, cu, s + k, &ctr->err);
+  }
+}
+
+// Phases 2 and 5: every parent becomes the root.
+__global__ void flatten_kernel(int* p, int* out, long long n, Counters* ctr) {   // out may equal p
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    out[v] = uf_find(p, (int)v, &ctr->err);
+}
+
+// Phase 3: the most frequent root among 1024 sampled vertices (one block
+// of 1024 threads: sample, bitonic sort in shared memory, longest run).
+__global__ void __launch_bounds__(1024) giant_kernel(const int* p, long long n, Counters* ctr) {
+  __shared__ int a[1024];
+  const unsigned t = threadIdx.x;
+  const unsigned long long x = ((unsigned long long)hash32(t * 2654435761u + 0x9E37u) * (unsigned long long)n) >> 32;
+  a[t] = __ldcg(p + x);
+  __syncthreads();
+  for (unsigned k = 2; k <= 1024; k <<= 1) {
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      const unsigned q = t ^ j;
+      if (q > t) {
+        const bool up = (t & k) == 0;
+        const int x0 = a[t], x1 = a[q];
+        if ((x0 > x1) == up) {
+          a[t] = x1;
+          a[q] = x0;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (t == 0) {
+    int best = a[0], best_run = 0, run = 0;
+    for (int i = 0; i < 1024; ++i) {
+      run = (i > 0 && a[i] == a[i - 1]) ? run + 1 : 1;
+      if (run > best_run) {
+        best_run = run;
+        best = a[i];
+      }
+    }
+    ctr->giant = best;
+  }
+}
+
+// Phase 4, classes 0..7: G lanes per vertex; vertices already in the
+// largest piece are skipped, the others offer entries SPLIT_SAMPLE.. of
+// their row (both directions: the other end may be skipped).
 template <int G>
 __global__ void __launch_bounds__(256) hook_group_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                                           const int* __restrict__ labels, int* p, long long n,
                                                           const int* __restrict__ work, Counters* ctr, int cls) {
   const unsigned cnt = (unsigned)ctr->cls_total[cls];
   const int* w = work + ctr->cls_start[cls];
+  const int giant = ctr->giant;
   const int gl = threadIdx.x & (G - 1);
   const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const long long ng = ((long long)gridDim.x * blockDim.x) / G;
   for (long long item = gid; item < (long long)cnt; item += ng) {
     const int u = w[item];
     const long long s = off[u], e = off[u + 1];
+    if (e - s <= SPLIT_SAMPLE || __ldcg(p + u) == giant) continue;
     const int cu = labels[u];
-    for (long long k = s + gl; k < e; k += G) hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
+    for (long long k = s + SPLIT_SAMPLE + gl; k < e; k += G) hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
   }
 }
 
-// Classes 7..8: one block per vertex.
+// Phase 4, classes 8..9: one block per vertex.
 __global__ void __launch_bounds__(512) hook_block_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                                           const int* __restrict__ labels, int* p, long long n,
                                                           const int* __restrict__ work, Counters* ctr, int cls) {
   const unsigned cnt = (unsigned)ctr->cls_total[cls];
   const int* w = work + ctr->cls_start[cls];
+  const int giant = ctr->giant;
+  __shared__ int s_skip;
   for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
     const int u = w[item];
     const long long s = off[u], e = off[u + 1];
+    if (threadIdx.x == 0) s_skip = __ldcg(p + u) == giant;
+    __syncthreads();
+    const int skip = s_skip;
+    __syncthreads();
+    if (skip) continue;
     const int cu = labels[u];
-    for (long long k = s + threadIdx.x; k < e; k += blockDim.x) hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
+    for (long long k = s + SPLIT_SAMPLE + threadIdx.x; k < e; k += blockDim.x)
+      hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
   }
-}
-
-__global__ void compress_kernel(int* p, int* __restrict__ out, long long n, Counters* ctr) {
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
-    out[v] = uf_find(p, (int)v, &ctr->err);
 }
 
 // ---------------------------------------------------------------- renumber
@@ -203,6 +270,9 @@ cudaError_t launch_split(const long long* off, const int* col, long long n, cons
   (void)t;
   if (n <= 0) return cudaSuccess;
   init_parent_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, n);
+  sample_link_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(off, col, labels, parent, n, ctr);
+  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, parent, n, ctr);
+  giant_kernel<<<1, 1024, 0, s>>>(parent, n, ctr);
   const int g = 8 * di.sm_count;
   hook_group_kernel<1><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 0);
   hook_group_kernel<2><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 1);
@@ -210,11 +280,12 @@ cudaError_t launch_split(const long long* off, const int* col, long long n, cons
   hook_group_kernel<8><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 3);
   hook_group_kernel<16><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 4);
   hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 5);
-  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP);
+  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_S);
+  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_L);
   hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_BLOCK);
   hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_HUB);
-  compress_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr);
-  count_launches(11);
+  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr);
+  count_launches(15);
   return cudaGetLastError();
 }
 
