@@ -176,6 +176,29 @@ int gsl_gsllpa(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, double to
                int32_t max_iters, int32_t mode, int32_t* labels_out, gsl_stats* stats,
                void* stream);
 
+/* Batched GSL-LPA: many independent graphs in one call.  The graphs are
+ * packed into one CSR `g` (their disjoint union): graph k owns vertices
+ * [vptr[k], vptr[k+1]) and its rows may only hold those vertices
+ * (GSL_ERR_INVALID otherwise).  Every graph gets exactly what gsl_gsllpa
+ * would give it alone -- its own change count, its own stop test
+ * dN_k / N_k <= tolerance, its own number of sweeps -- and labels_out holds,
+ * for every vertex, the smallest LOCAL vertex id (id - vptr[k]) of its
+ * connected community piece.  The whole sweep loop runs as one CUDA graph
+ * launch (captured on first use, replayed while the arguments are the same);
+ * sweeps after every graph has stopped return at once.
+ *   vptr_host       HOST int64[num_graphs+1], vptr[0] = 0, vptr[num_graphs] = n.
+ *   iterations_out  optional HOST int32[num_graphs]: sweeps per graph.
+ *   stats           optional. */
+typedef struct gsl_batch_stats {
+  int32_t num_graphs;
+  int32_t pad;
+  int64_t graph_launches;   /* CUDA graph launches used by the sweep loop (1) */
+  float ms;                 /* device time of the call                        */
+} gsl_batch_stats;
+int gsl_gsllpa_batch(gsl_ctx* ctx, const gsl_csr* g, int32_t num_graphs, const int64_t* vptr_host,
+                     const int32_t* weights, double tolerance, int32_t max_iters, int32_t mode,
+                     int32_t* labels_out, int32_t* iterations_out, gsl_batch_stats* stats, void* stream);
+
 /* gsl_gsllpa on HOST buffers: copies offsets, cols and weights (nullable) to
  * the device, runs GSL-LPA and copies the labels back to labels_out_host
  * (host int32[n]).  Device copies of the graph are context scratch.  Host

@@ -49,6 +49,11 @@ class Profile(ctypes.Structure):
     _fields_ = [("nslots", ctypes.c_int32), ("slot", ProfileSlot * 24)]
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("num_graphs", ctypes.c_int32), ("pad", ctypes.c_int32), ("graph_launches", ctypes.c_int64),
+                ("ms", ctypes.c_float)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("changed", ctypes.c_int64 * STATS_SWEEPS), ("active", ctypes.c_int64 * STATS_SWEEPS),
@@ -92,6 +97,7 @@ def load():
         lib.gsl_modularity.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
         lib.gsl_gsllpa.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
         lib.gsl_gsllpa_host.argtypes = [P, i64, i64, P, P, P, dbl, i32, i32, P, sp, P]
+        lib.gsl_gsllpa_batch.argtypes = [P, cp, i32, P, P, dbl, i32, i32, P, P, ctypes.POINTER(BatchStats), P]
         lib.gsl_strerror.restype = ctypes.c_char_p
         lib.gsl_strerror.argtypes = [ctypes.c_int]
         lib.gsl_ctx_last_error.restype = ctypes.c_char_p
@@ -103,7 +109,7 @@ def load():
         lib.gsl_kernel_launches.argtypes = []
         for name in ("gsl_ctx_create", "gsl_ctx_destroy", "gsl_ctx_set_tuning", "gsl_lpa", "gsl_split",
                      "gsl_ctx_set_profiling", "gsl_ctx_get_profile",
-                     "gsl_modularity", "gsl_gsllpa", "gsl_gsllpa_host"):
+                     "gsl_modularity", "gsl_gsllpa", "gsl_gsllpa_host", "gsl_gsllpa_batch"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -224,6 +230,27 @@ class Context:
                                   int(mode), _ptr(out), ctypes.byref(st), _stream(stream))
         self._raise(rc)
         return (out, st.as_dict()) if stats else out
+
+    def gsllpa_batch(self, offsets, cols, vptr, weights=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC,
+                     out=None, stream=None, stats=False):
+        """Batched GSL-LPA over graphs packed in one CSR (graph k owns vertices
+        vptr[k]..vptr[k+1]-1).  Returns local labels (and per-graph sweeps)."""
+        import numpy as np
+        import torch
+        g = _check_graph(offsets, cols, weights)
+        vp = np.ascontiguousarray(np.asarray(vptr, dtype=np.int64))
+        ng = int(vp.shape[0] - 1)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        iters = np.zeros(max(ng, 1), dtype=np.int32)
+        bs = BatchStats()
+        rc = self._lib.gsl_gsllpa_batch(self._h, ctypes.byref(g), ng, vp.ctypes.data_as(ctypes.c_void_p), _ptr(weights),
+                                        float(tolerance), int(max_iters), int(mode), _ptr(out),
+                                        iters.ctypes.data_as(ctypes.c_void_p), ctypes.byref(bs), _stream(stream))
+        self._raise(rc)
+        if stats:
+            return out, iters[:ng].copy(), {"ms": bs.ms, "graph_launches": bs.graph_launches}
+        return out, iters[:ng].copy()
 
     def gsllpa_host(self, offsets, cols, weights=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC, out=None,
                     stream=None, stats=False):

@@ -60,6 +60,25 @@ struct gsl_ctx {
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
+  // batched mode
+  int* gid = nullptr;
+  long long cap_gid = 0;
+  long long* vptr = nullptr;
+  long long cap_vptr = 0;
+  unsigned* dn_graph = nullptr;
+  long long cap_dng = 0;
+  int* iters = nullptr;
+  long long cap_iters = 0;
+  unsigned char* done = nullptr;
+  long long cap_done = 0;
+  int* stop = nullptr;
+  long long cap_stop = 0;
+  int* lab_tmp = nullptr;
+  long long cap_lab_tmp = 0;
+  cudaStream_t cap_stream = nullptr;   // captures and replays the batched sweep loop
+  cudaGraphExec_t batch_exec = nullptr;
+  std::vector<long long> batch_key;    // arguments the captured graph was built for
+
   // profiling (gsl_ctx_set_profiling): CUDA-event time per launch sequence
   bool prof = false;
   gsl_profile profile{};
@@ -509,6 +528,11 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->evpool) cudaEventDestroy(e);
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  void* bptrs[] = {c->gid, c->vptr, c->dn_graph, c->iters, c->done, c->stop, c->lab_tmp};
+  for (void* p : bptrs)
+    if (p) cudaFree(p);
   delete c;
   return GSL_OK;
 }
@@ -625,6 +649,132 @@ int gsl_gsllpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, double tol,
     cudaEventElapsedTime(&st->ms_lpa, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&st->ms_split, c->ev[1], c->ev[2]);
     st->communities = k;
+  }
+  return GSL_OK;
+}
+
+int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int64_t* vptr_host,
+                     const int32_t* weights, double tol, int32_t max_iters, int32_t mode, int32_t* labels_out,
+                     int32_t* iterations_out, gsl_batch_stats* st, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_lpa_args(c, g, tol, max_iters, mode, labels_out)) return r;
+  if (num_graphs < 1 || !vptr_host) return fail(c, GSL_ERR_INVALID, "need num_graphs >= 1 and vptr");
+  if (vptr_host[0] != 0 || vptr_host[num_graphs] != g->n)
+    return fail(c, GSL_ERR_INVALID, "vptr must start at 0 and end at n");
+  for (int k = 0; k < num_graphs; ++k)
+    if (vptr_host[k + 1] < vptr_host[k]) return fail(c, GSL_ERR_INVALID, "vptr must be nondecreasing");
+  if (st) memset(st, 0, sizeof(*st));
+  const long long n = g->n;
+  const bool async_mode = mode == GSL_MODE_ASYNC;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (int r = ensure_vertex_scratch(c, n > 0 ? n : 1)) return r;
+  if (int r = grow(c, c->gid, c->cap_gid, n)) return r;
+  if (int r = grow(c, c->lab_tmp, c->cap_lab_tmp, n)) return r;
+  if (int r = grow(c, c->vptr, c->cap_vptr, (long long)num_graphs + 1)) return r;
+  if (int r = grow(c, c->dn_graph, c->cap_dng, num_graphs)) return r;
+  if (int r = grow(c, c->iters, c->cap_iters, num_graphs)) return r;
+  if (int r = grow(c, c->done, c->cap_done, num_graphs)) return r;
+  if (int r = grow(c, c->stop, c->cap_stop, 1)) return r;
+  CK(cudaEventRecord(c->ev[0], s));
+  CK(cudaMemcpyAsync(c->vptr, vptr_host, sizeof(int64_t) * (size_t)(num_graphs + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_fill_gid(c->vptr, num_graphs, n, c->gid, c->di, s));
+  if (n > 0)
+    if (int r = prepare_graph(c, g, s)) return r;
+  CK(cudaMemsetAsync(c->done, 0, (size_t)num_graphs, s));
+  CK(cudaMemsetAsync(c->iters, 0, sizeof(int) * (size_t)num_graphs, s));
+  CK(cudaMemsetAsync(c->stop, 0, sizeof(int), s));
+  CK(launch_graph_update(0, tol, max_iters, c->vptr, num_graphs, c->dn_graph, c->iters, c->done, c->stop, s));
+  // The sweep loop, unrolled over max_iters and captured once as a CUDA
+  // graph; sweeps after the last graph stops return at once.
+  const std::vector<long long> key = {(long long)OFF(g), (long long)g->cols, (long long)weights, n, g->nnz,
+                                      num_graphs, max_iters, mode, (long long)(tol * 1e12), c->ctr_h->max_degree,
+                                      (long long)c->lab[0], (long long)c->wtab, (long long)c->btab};
+  long long graph_launches = 0;
+  if (n > 0) {
+    if (!c->batch_exec || c->batch_key != key) {
+      if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+      c->batch_exec = nullptr;
+      cudaStream_t cs = c->cap_stream;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      cudaError_t cerr = cudaSuccess;
+      auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && cerr == cudaSuccess) cerr = e;
+      };
+      ck(cudaMemsetAsync(c->flag[0], 0, (size_t)n, cs));
+      ck(cudaMemsetAsync(c->flag[1], 0, (size_t)n, cs));
+      ck(launch_init_labels(nullptr, c->lab[0], async_mode ? nullptr : c->lab[1], n, c->ctr, c->di, cs));
+      SweepArgs a{};
+      a.off = OFF(g);
+      a.col = g->cols;
+      a.w = weights;
+      a.ctr = c->ctr;
+      a.work = c->work;
+      a.wtab = c->wtab;
+      a.wtab_region = 2ll * c->tune.warp_max;
+      a.btab = c->btab;
+      a.btab_region = 2ll * c->ctr_h->max_degree;
+      a.n = n;
+      a.gid = c->gid;
+      a.vptr = c->vptr;
+      a.dn_graph = c->dn_graph;
+      a.stop = c->stop;
+      for (int t = 1; t <= max_iters; ++t) {
+        ck(cudaMemsetAsync(c->ctr, 0, offsetof(Counters, err), cs));
+        ck(cudaMemsetAsync(c->dn_graph, 0, sizeof(unsigned) * (size_t)num_graphs, cs));
+        ck(launch_bin(OFF(g), n, c->flag[t & 1], t <= 2 ? 1 : 0, c->tune, c->work, c->ctr, c->di, cs, c->gid,
+                      c->done, c->stop));
+        a.prev = async_mode ? c->lab[0] : c->lab[(t - 1) & 1];
+        a.next = async_mode ? c->lab[0] : c->lab[t & 1];
+        a.fnext = c->flag[(t + 1) & 1];
+        a.ident = (!async_mode && t == 1) ? 1 : 0;
+        a.check = t == 1 ? 1 : 0;
+        a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
+        a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
+        for (int k = 0; k < NCLASS; ++k) ck(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, cs));
+        ck(launch_graph_update(t, tol, max_iters, c->vptr, num_graphs, c->dn_graph, c->iters, c->done, c->stop, cs));
+      }
+      const int* bufs[2] = {c->lab[0], c->lab[1]};
+      ck(launch_batch_final(bufs, c->iters, c->gid, n, async_mode ? 1 : 0, c->lab_tmp, c->di, cs));
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e_end = cudaStreamEndCapture(cs, &graph);
+      if (cerr != cudaSuccess || e_end != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(c, GSL_ERR_CUDA, "capturing the batched sweep loop failed: %s",
+                    cudaGetErrorString(cerr != cudaSuccess ? cerr : e_end));
+      }
+      const cudaError_t e_inst = cudaGraphInstantiate(&c->batch_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e_inst != cudaSuccess) {
+        cudaGetLastError();
+        c->batch_exec = nullptr;
+        return fail(c, GSL_ERR_CUDA, "instantiating the batched sweep loop failed: %s", cudaGetErrorString(e_inst));
+      }
+      c->batch_key = key;
+    }
+    CK(cudaEventRecord(c->ev[3], s));
+    CK(cudaStreamWaitEvent(c->cap_stream, c->ev[3], 0));
+    CK(cudaGraphLaunch(c->batch_exec, c->cap_stream));
+    graph_launches = 1;
+    CK(cudaEventRecord(c->ev[3], c->cap_stream));
+    CK(cudaStreamWaitEvent(s, c->ev[3], 0));
+    CK(cudaEventRecord(c->ev[1], s));
+    long long k = 0;
+    if (int r = run_split(c, g, c->lab_tmp, labels_out, 0, &k, s)) return r;
+    CK(launch_localize(c->vptr, c->gid, n, labels_out, c->di, s));
+  }
+  if (iterations_out)
+    CK(cudaMemcpyAsync(iterations_out, c->iters, sizeof(int32_t) * (size_t)num_graphs, cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(c->ev[2], s));
+  CK(cudaEventSynchronize(c->ev[2]));
+  if (int r = map_err(c, c->ctr_h->err, "batch")) return r;
+  if (st) {
+    cudaEventElapsedTime(&st->ms, c->ev[0], c->ev[2]);
+    st->graph_launches = graph_launches;
+    st->num_graphs = num_graphs;
   }
   return GSL_OK;
 }

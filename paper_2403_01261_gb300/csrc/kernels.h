@@ -22,6 +22,11 @@ struct SweepArgs {
   long long btab_region;     // slots per block region (2 * largest degree of classes 7-8)
   long long n;
   int gthresh;               // hub degree above which the block kernel goes straight to global tables (0: never)
+  // batched mode (many graphs packed in one CSR); all null for one graph
+  const int* gid;            // graph of every vertex
+  const long long* vptr;     // vertex range of every graph [vptr[g], vptr[g+1])
+  unsigned* dn_graph;        // per-graph change count of this sweep
+  const int* stop;           // nonzero: every graph is done, kernels return at once
   int ident;                 // prev is the identity labelling (not read)
   int check;                 // validate weights and weighted degrees
   int mark;                  // mark neighbours of changed vertices in fnext
@@ -53,7 +58,8 @@ struct DeviceInfo {
 cudaError_t launch_class_histogram(const long long* off, long long n, long long nnz, const Tuning& t,
                                    Counters* ctr, const DeviceInfo& di, cudaStream_t s);
 cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, int all_active,
-                       const Tuning& t, int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+                       const Tuning& t, int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s,
+                       const int* gid = nullptr, const unsigned char* done = nullptr, const int* stop = nullptr);
 cudaError_t launch_sweep(const SweepArgs& a, bool weighted, bool async_mode, const Tuning& t,
                          const DeviceInfo& di, cudaStream_t s);
 cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool async_mode, const Tuning& t,
@@ -65,6 +71,17 @@ cudaError_t launch_init_labels(const int* init, int* a, int* b, long long n, Cou
 long long block_grid_size(const Tuning& t, const DeviceInfo& di);   // blocks of the class 8/9 kernel
 long long warp_grid_warps(const Tuning& t, const DeviceInfo& di);   // warps of the class 7 kernel
 ClassBounds class_bounds(const Tuning& t);
+
+// batch_kernels.cu
+cudaError_t launch_fill_gid(const long long* vptr, int num_graphs, long long n, int* gid, const DeviceInfo& di,
+                            cudaStream_t s);
+cudaError_t launch_graph_update(int t, double tol, int max_iters, const long long* vptr, int num_graphs,
+                                const unsigned* dn_graph, int* iters, unsigned char* done, int* stop,
+                                cudaStream_t s);
+cudaError_t launch_batch_final(const int* const* bufs, const int* iters, const int* gid, long long n, int async_mode,
+                               int* out, const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_localize(const long long* vptr, const int* gid, long long n, int* labels, const DeviceInfo& di,
+                            cudaStream_t s);
 
 // split_kernels.cu
 cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels,

@@ -110,6 +110,19 @@ __device__ __forceinline__ void load_entry(const SweepArgs& a, const int* cp, co
   }
 }
 
+// Batched mode, first sweep: every column of a row must lie in the row's
+// own graph (a packed batch has no edges between graphs).
+__device__ __forceinline__ void check_same_graph(const SweepArgs& a, int v, int j) {
+  if (a.gid && a.check && j >= 0 && __ldg(a.gid + j) != __ldg(a.gid + v)) raise_err(&a.ctr->err, ERRBIT_INVALID);
+}
+
+// Batched mode: per-graph change count.
+__device__ __forceinline__ void count_graph_change(const SweepArgs& a, int v) {
+  if (a.dn_graph) atomicAdd(a.dn_graph + a.gid[v], 1u);
+}
+
+__device__ __forceinline__ bool stopped(const SweepArgs& a) { return a.stop && *(volatile const int*)a.stop; }
+
 template <bool ASYNC>
 __device__ __forceinline__ int gather_label(const SweepArgs& a, int j, const Pol& pol) {
   if (a.ident) return j;
@@ -180,7 +193,9 @@ constexpr int BIN_ITEMS = 8;
 
 __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ off, long long n,
                                                    unsigned char* __restrict__ fcur, int all_active, ClassBounds cb,
-                                                   int* __restrict__ work, Counters* ctr) {
+                                                   int* __restrict__ work, Counters* ctr, const int* __restrict__ gid,
+                                                   const unsigned char* __restrict__ done, const int* stop) {
+  if (stop && *(volatile const int*)stop) return;
   __shared__ unsigned cnt[NCLASS];
   __shared__ unsigned base[NCLASS];
   const long long tile = (long long)blockDim.x * BIN_ITEMS;
@@ -196,6 +211,7 @@ __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ 
       if (v < n) {
         bool act = all_active != 0;
         if (!act && fcur[v]) { act = true; fcur[v] = 0; }
+        if (act && gid && done[gid[v]]) act = false;   // batched: this vertex's graph has stopped
         if (act) cls[k] = degree_class(off[v + 1] - off[v], cb.warp_small, cb.warp_max, cb.blk_max);
       }
       if (cls[k] >= 0) pos[k] = atomicAdd(&cnt[cls[k]], 1u);
@@ -234,6 +250,7 @@ __global__ void init_labels_kernel(const int* __restrict__ init, int* __restrict
 // Classes 0..5: G lanes per vertex, 32/G vertices per warp per step.
 template <int G, bool WEIGHTED, bool ASYNC>
 __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) {
+  if (stopped(a)) return;
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
   const Pol pol = make_pol();
@@ -258,6 +275,7 @@ __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) 
     }
     int j, wt;
     load_entry<WEIGHTED>(a, a.col + s, a.w + s, d, gl, pol, j, wt);
+    check_same_graph(a, v, j);
     const bool nb = j >= 0;
     const bool valid = nb && j != v;       // scanCommunities skips j == i
     const int lbl = valid ? gather_label<ASYNC>(a, j, pol) : -1;
@@ -279,6 +297,7 @@ __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) 
       const int nl = mc ? (int)~binv : old;
       changed = nl != old;
       store_label<ASYNC>(a, v, nl, changed);
+      if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;
       my_dn += changed ? 1ull : 0ull;
     }
@@ -305,19 +324,28 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
   bool sorted = true;
   const int* cp = a.col + s;
   const int* wp = a.w + s;
-  const int lane = tid & 31;
-  for (int e0 = (tid & ~31); e0 < d; e0 += (nthreads & ~31)) {
-    int j, wt;
-    load_entry<WEIGHTED>(a, cp, wp, d, e0 + lane, pol, j, wt);
-    int nxt = __shfl_down_sync(FULL, j, 1);
-    if (lane == 31 && e0 + 32 < d) nxt = ld_stream(cp + e0 + 32, pol.stream);
-    if (j >= 0 && e0 + lane + 1 < d && !(j < nxt)) sorted = false;
-    if (j < 0 && e0 + lane < d) sorted = false;      // invalid entry: let the hash path handle it
-    if (j >= 0) {
-      wsum += (unsigned long long)wt;
-      if (j != v) {
-        const unsigned long long k = pack_key((unsigned)wt, j);
-        best = k > best ? k : best;
+  const int lane = tid & 31, wid = tid >> 5, nw = nthreads >> 5;
+  // each warp takes 128-entry rounds: four chunks in flight per lane
+  for (int e0 = wid * 128; e0 < d; e0 += nw * 128) {
+    int j[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
+    const int tail = (lane == 31 && e0 + 128 < d) ? ld_stream(cp + e0 + 128, pol.stream) : 0x7FFFFFFF;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + 32 * u + lane;
+      int nxt = __shfl_down_sync(FULL, j[u], 1);
+      const int head = u < 3 ? __shfl_sync(FULL, j[u < 3 ? u + 1 : u], 0) : tail;
+      if (lane == 31) nxt = head;
+      check_same_graph(a, v, j[u]);
+      if (j[u] >= 0 && e + 1 < d && !(j[u] < nxt)) sorted = false;
+      if (j[u] < 0 && e < d) sorted = false;      // invalid entry: let the hash path handle it
+      if (j[u] >= 0) {
+        wsum += (unsigned long long)w[u];
+        if (j[u] != v) {
+          const unsigned long long k = pack_key((unsigned)w[u], j[u]);
+          best = k > best ? k : best;
+        }
       }
     }
   }
@@ -354,43 +382,104 @@ __device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned c
   return 0;
 }
 
+// Inserts one 128-entry round -- four 32-entry chunks of labels l[u] and
+// weights w[u] -- into `tab`.  Equal labels within a chunk are merged with
+// __match_any_sync; when the round has at most 32 distinct (chunk, label)
+// pairs, the pairs of all four chunks are compacted into one warp (through
+// the warp's 32-slot `stage`) and merged again, so that each distinct label
+// of the round costs one table update.  Returns the slots created
+// (warp-uniform).
+template <bool WEIGHTED, bool GLOBAL>
+__device__ __forceinline__ unsigned insert_round(unsigned long long* tab, unsigned cap, const int (&l)[4],
+                                                 const int (&w)[4], int nchunks, unsigned long long* stage,
+                                                 unsigned long long& best, int* err) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  unsigned lead[4], cnt[4];
+  unsigned total = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    lead[u] = 0;
+    cnt[u] = 0;
+    if (u < nchunks) {
+      const unsigned m = __match_any_sync(FULL, l[u]);
+      cnt[u] = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+      lead[u] = __ballot_sync(FULL, l[u] >= 0 && (m & lt) == 0);
+      total += __popc(lead[u]);
+    }
+  }
+  unsigned made = 0;
+  if (total <= 32) {
+    unsigned base = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if ((lead[u] >> lane) & 1u) stage[base + __popc(lead[u] & lt)] = ((unsigned long long)(unsigned)l[u] << 32) | cnt[u];
+      base += __popc(lead[u]);
+    }
+    __syncwarp();
+    const bool has = lane < (int)total;
+    const unsigned long long pr = has ? stage[lane] : 0ull;
+    __syncwarp();
+    const int ml = has ? (int)(pr >> 32) : -1;
+    const unsigned m2 = __match_any_sync(FULL, ml);
+    const unsigned c2 = __reduce_add_sync(m2, (unsigned)pr);
+    bool created = false;
+    if (has && (m2 & lt) == 0) {
+      const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)ml, c2, created, err);
+      const unsigned long long k = pack_key(sum, ml);
+      best = k > best ? k : best;
+    }
+    made = __popc(__ballot_sync(FULL, created));
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      bool created = false;
+      if ((lead[u] >> lane) & 1u) {
+        const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], cnt[u], created, err);
+        const unsigned long long k = pack_key(sum, l[u]);
+        best = k > best ? k : best;
+      }
+      made += __popc(__ballot_sync(FULL, created));
+    }
+  }
+  return made;
+}
+
+// Loads one 128-entry round of row (cp, wp, d) starting at e0: columns and
+// weights of four chunks first, then their labels, so that each lane has
+// eight loads in flight.
+template <bool WEIGHTED, bool ASYNC>
+__device__ __forceinline__ void load_round(const SweepArgs& a, int v, const int* cp, const int* wp, int d, int e0,
+                                           const Pol& pol, int (&l)[4], int (&w)[4], unsigned long long& wsum) {
+  const int lane = threadIdx.x & 31;
+  int j[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    check_same_graph(a, v, j[u]);
+    if (j[u] >= 0) wsum += (unsigned long long)w[u];
+    l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
+  }
+}
+
 // One warp aggregates the row (cp, wp, d) of vertex v into `tab` (cap
-// slots).  Four 32-entry chunks are loaded (columns, then labels) before any
-// is hashed, so each lane keeps eight loads in flight.  Within a chunk equal
-// labels are merged with __match_any_sync and only the lowest lane of each
-// group inserts.  Returns true (warp-uniform) once more than `limit`
-// distinct labels have been inserted: the table is then abandoned.
+// slots).  Returns true (warp-uniform) once more than `limit` distinct
+// labels have been inserted: the table is then abandoned.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
-                                         unsigned long long& best, unsigned long long& wsum) {
+                                         unsigned long long* stage, unsigned long long& best,
+                                         unsigned long long& wsum) {
   const int lane = threadIdx.x & 31;
   for (unsigned k = lane; k < cap; k += 32) tab[k] = EMPTY64;
   __syncwarp();
   unsigned used = 0;
   for (int e0 = 0; e0 < d; e0 += 128) {
-    int j[4], w[4], l[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (j[u] >= 0) wsum += (unsigned long long)w[u];
-      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
-        const unsigned m = __match_any_sync(FULL, l[u]);
-        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
-        bool created = false;
-        if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
-          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
-          const unsigned long long k = pack_key(sum, l[u]);
-          best = k > best ? k : best;
-        }
-        if (limit != 0xFFFFFFFFu) used += __popc(__ballot_sync(FULL, created));
-      }
-    }
+    int l[4], w[4];
+    load_round<WEIGHTED, ASYNC>(a, v, cp, wp, d, e0, pol, l, w, wsum);
+    const int nchunks = (d - e0 + 31) >> 5;
+    used += insert_round<WEIGHTED, GLOBAL>(tab, cap, l, w, nchunks, stage, best, &a.ctr->err);
     if (used > limit) return true;   // at most 128 slots past the limit
   }
   return false;
@@ -403,7 +492,10 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, const int* c
 // worklist entry and offsets are loaded while the current one is processed.
 template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL>
 __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
+  if (stopped(a)) return;
   extern __shared__ unsigned long long smem_w64[];
+  __shared__ unsigned long long s_stage[8][32];
+  unsigned long long* stage = s_stage[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   unsigned long long* tab = smem_w64 + (size_t)(threadIdx.x >> 5) * TW;
   const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -443,10 +535,10 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
       const unsigned want = 2u * (unsigned)d;
       const unsigned cap = want < (unsigned)TW ? want : (unsigned)TW;
       const unsigned limit = (!SPILL || cap >= want) ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
-      if (warp_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, tab, cap, limit, pol, best, wsum) && SPILL) {
+      if (warp_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, tab, cap, limit, pol, stage, best, wsum) && SPILL) {
         best = 0;
         wsum = 0;
-        warp_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum);
+        warp_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, stage, best, wsum);
       }
       __syncwarp();
     }
@@ -459,6 +551,7 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
     const bool changed = nl != old;
     if (lane == 0) {
       store_label<ASYNC>(a, v, nl, changed);
+      if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;
       my_dn += changed ? 1ull : 0ull;
     }
@@ -475,14 +568,15 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
 }
 
 // One block aggregates the row of v into `tab`; every warp takes 128-entry
-// chunks.  Before each chunk a warp checks the block's overflow flag, and
-// after it adds its new slots to the block's count; past `limit` the flag
-// is raised.  Returns the flag (block-uniform after the barrier).
+// rounds.  Before each round a warp checks the block's overflow flag, and
+// after it adds its new slots to the block's count; past `limit` the flag is
+// raised (each of the block's warps may add one more round, at most 128
+// slots, before it sees the flag).  Returns the flag (block-uniform).
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
-                                         unsigned long long& best, unsigned long long& wsum, unsigned* s_used,
-                                         volatile int* s_ovf) {
+                                         unsigned long long* stage, unsigned long long& best,
+                                         unsigned long long& wsum, unsigned* s_used, volatile int* s_ovf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
   if (threadIdx.x == 0) {
@@ -491,37 +585,12 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* c
   }
   __syncthreads();
   for (int e0 = wid * 128; e0 < d; e0 += nw * 128) {
-    int j[4], w[4], l[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (j[u] >= 0) wsum += (unsigned long long)w[u];
-      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
-    }
-    bool stop = false;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (!stop && e0 + 32 * u < d) {
-        if (limit != 0xFFFFFFFFu && __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0)) {
-          stop = true;
-        } else {
-          const unsigned m = __match_any_sync(FULL, l[u]);
-          const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
-          bool created = false;
-          if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
-            const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
-            const unsigned long long k = pack_key(sum, l[u]);
-            best = k > best ? k : best;
-          }
-          if (limit != 0xFFFFFFFFu) {
-            const unsigned nc = __popc(__ballot_sync(FULL, created));
-            if (lane == 0 && nc && atomicAdd(s_used, nc) + nc > limit) *s_ovf = 1;
-          }
-        }
-      }
-    }
-    if (stop) break;
+    if (limit != 0xFFFFFFFFu && __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0)) break;
+    int l[4], w[4];
+    load_round<WEIGHTED, ASYNC>(a, v, cp, wp, d, e0, pol, l, w, wsum);
+    const int nchunks = (d - e0 + 31) >> 5;
+    const unsigned made = insert_round<WEIGHTED, GLOBAL>(tab, cap, l, w, nchunks, stage, best, &a.ctr->err);
+    if (limit != 0xFFFFFFFFu && lane == 0 && made && atomicAdd(s_used, made) + made > limit) *s_ovf = 1;
   }
   __syncthreads();
   return *s_ovf;
@@ -533,7 +602,10 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* c
 // fallback tables instead (a.btab_region slots).
 template <bool WEIGHTED, bool ASYNC>
 __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, unsigned tb, int gthresh) {
+  if (stopped(a)) return;
   extern __shared__ unsigned long long smem_b64[];
+  __shared__ unsigned long long s_stage[16][32];
+  unsigned long long* stage = s_stage[threadIdx.x >> 5];
   __shared__ unsigned long long s_best, s_wsum;
   __shared__ unsigned s_used;
   __shared__ int s_ovf, s_changed;
@@ -564,14 +636,17 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
       int ovf = 1;
       if (!(gthresh > 0 && d > gthresh)) {
         const unsigned cap = want < tb ? want : tb;
-        const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, smem_b64, cap, limit, pol, best, wsum, &s_used,
-                                                &s_ovf);
+        // up to 16 warps x 128 new slots may land after the flag is raised;
+        // a half-full table keeps linear probes short
+        const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 2;
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, smem_b64, cap, limit, pol, stage, best, wsum,
+                                                &s_used, &s_ovf);
       }
       if (ovf) {
         best = 0;
         wsum = 0;
-        block_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, &s_used, &s_ovf);
+        block_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, stage, best, wsum, &s_used,
+                                         &s_ovf);
       }
     }
     best = warp_max_u64(best);
@@ -587,6 +662,7 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
       const int nl = s_best ? (int)~(unsigned)s_best : old;
       const bool changed = nl != old;
       store_label<ASYNC>(a, v, nl, changed);
+      if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;
       my_dn += changed ? 1ull : 0ull;
       s_changed = changed;
@@ -733,12 +809,14 @@ cudaError_t launch_class_histogram(const long long* off, long long n, long long 
 }
 
 cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, int all_active, const Tuning& t,
-                       int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+                       int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s, const int* gid,
+                       const unsigned char* done, const int* stop) {
   if (n <= 0) return cudaSuccess;
   const long long tile = 256ll * BIN_ITEMS;
   long long blocks = (n + tile - 1) / tile;
   const long long cap = 8ll * di.sm_count;
-  bin_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr);
+  bin_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr,
+                                                                 gid, done, stop);
   count_launches(1);
   return cudaGetLastError();
 }
