@@ -199,6 +199,70 @@ int gsl_gsllpa_batch(gsl_ctx* ctx, const gsl_csr* g, int32_t num_graphs, const i
                      const int32_t* weights, double tolerance, int32_t max_iters, int32_t mode,
                      int32_t* labels_out, int32_t* iterations_out, gsl_batch_stats* stats, void* stream);
 
+/* How gsl_gsllpa_batch runs its sweep loop: 1 (default) as one CUDA graph,
+ * captured on first use and replayed while the arguments repeat; 0 as
+ * direct kernel launches (better when every call has a new shape, as in the
+ * request server).  Results are the same. */
+int gsl_ctx_set_batch_mode(gsl_ctx* ctx, int32_t use_cuda_graph);
+
+/* ---------------------------------------------------------------------
+ * Request server with continuous batching.
+ *
+ * Each request is one graph (HOST CSR).  The server runs `slots` workers,
+ * each with its own context, CUDA stream and device buffers that stay
+ * resident for the server's life.  A free worker admits the oldest waiting
+ * requests that fit its buffers (admission by device memory), packs them
+ * into one batch CSR on the device and runs gsl_gsllpa_batch on it; requests
+ * that arrive while batches are running are admitted by the next worker to
+ * free up, so the work of different requests overlaps on the GPU.  Every
+ * request gets exactly its solo gsl_gsllpa result.
+ * --------------------------------------------------------------------- */
+typedef struct gsl_server gsl_server;
+
+typedef struct gsl_server_config {
+  int32_t device;
+  int32_t slots;              /* concurrent batches (workers), 1..64                       */
+  int64_t slot_vertices;      /* vertex capacity of one batch; 0: derived from free memory */
+  int64_t slot_entries;       /* CSR entry capacity of one batch; 0: derived               */
+  double memory_fraction;     /* share of free device memory used when deriving (0: 0.5)   */
+  int32_t max_batch_graphs;   /* graphs per batch (0: 1024; at most 65535)                 */
+  int32_t mode;               /* GSL_MODE_SYNC or GSL_MODE_ASYNC                           */
+  double tolerance;
+  int32_t max_iters;
+  int32_t pad;
+} gsl_server_config;
+
+typedef struct gsl_request_info {
+  int32_t status;             /* GSL_OK or an error code                                   */
+  int32_t sweeps;             /* sweeps performed for this graph                           */
+  int64_t batch_graphs;       /* graphs in the batch that served it                        */
+  double queue_ms;            /* submit -> admitted                                        */
+  double service_ms;          /* admitted -> labels on the host                            */
+  double latency_ms;          /* submit -> labels on the host                              */
+} gsl_request_info;
+
+typedef struct gsl_server_stats {
+  int64_t completed;
+  int64_t batches;
+  int64_t queued;
+  int64_t max_concurrent_batches;
+} gsl_server_stats;
+
+int gsl_server_create(gsl_server** server, const gsl_server_config* config);
+/* Largest graph (vertices, entries) a batch can hold. */
+int gsl_server_capacity(gsl_server* server, int64_t* max_vertices, int64_t* max_entries);
+/* Queues one graph.  offsets (n+1) and cols (nnz) are HOST buffers owned by
+ * the caller and must stay valid until gsl_server_wait returns for it.
+ * Thread safe.  GSL_ERR_NOMEM if the graph can never fit a batch. */
+int gsl_server_submit(gsl_server* server, int64_t n, int64_t nnz, const int64_t* offsets, const int32_t* cols,
+                      int64_t* request_id);
+/* Blocks until the request is done; labels_out (HOST int32[n], nullable)
+ * receives its connected-community labels.  Each id can be waited once. */
+int gsl_server_wait(gsl_server* server, int64_t request_id, int32_t* labels_out, gsl_request_info* info);
+int gsl_server_get_stats(gsl_server* server, gsl_server_stats* stats);
+/* Finishes every queued request, stops the workers and frees all memory. */
+int gsl_server_destroy(gsl_server* server);
+
 /* gsl_gsllpa on HOST buffers: copies offsets, cols and weights (nullable) to
  * the device, runs GSL-LPA and copies the labels back to labels_out_host
  * (host int32[n]).  Device copies of the graph are context scratch.  Host

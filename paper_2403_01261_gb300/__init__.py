@@ -18,7 +18,7 @@ import threading
 from . import _build
 
 __all__ = ["Stats", "Context", "GslError", "lpa", "split", "modularity", "gsllpa", "gsllpa_host", "library_path",
-           "load", "kernel_launches", "MODE_SYNC", "MODE_ASYNC"]
+           "load", "kernel_launches", "Server", "MODE_SYNC", "MODE_ASYNC"]
 
 MODE_SYNC = 0
 MODE_ASYNC = 1
@@ -52,6 +52,23 @@ class Profile(ctypes.Structure):
 class BatchStats(ctypes.Structure):
     _fields_ = [("num_graphs", ctypes.c_int32), ("pad", ctypes.c_int32), ("graph_launches", ctypes.c_int64),
                 ("ms", ctypes.c_float)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("slot_vertices", ctypes.c_int64),
+                ("slot_entries", ctypes.c_int64), ("memory_fraction", ctypes.c_double),
+                ("max_batch_graphs", ctypes.c_int32), ("mode", ctypes.c_int32), ("tolerance", ctypes.c_double),
+                ("max_iters", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("batch_graphs", ctypes.c_int64),
+                ("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("batches", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("max_concurrent_batches", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -98,6 +115,13 @@ def load():
         lib.gsl_gsllpa.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
         lib.gsl_gsllpa_host.argtypes = [P, i64, i64, P, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_gsllpa_batch.argtypes = [P, cp, i32, P, P, dbl, i32, i32, P, P, ctypes.POINTER(BatchStats), P]
+        lib.gsl_ctx_set_batch_mode.argtypes = [P, i32]
+        lib.gsl_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ServerConfig)]
+        lib.gsl_server_capacity.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.gsl_server_submit.argtypes = [P, i64, i64, P, P, ctypes.POINTER(i64)]
+        lib.gsl_server_wait.argtypes = [P, i64, P, ctypes.POINTER(RequestInfo)]
+        lib.gsl_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+        lib.gsl_server_destroy.argtypes = [P]
         lib.gsl_strerror.restype = ctypes.c_char_p
         lib.gsl_strerror.argtypes = [ctypes.c_int]
         lib.gsl_ctx_last_error.restype = ctypes.c_char_p
@@ -109,7 +133,9 @@ def load():
         lib.gsl_kernel_launches.argtypes = []
         for name in ("gsl_ctx_create", "gsl_ctx_destroy", "gsl_ctx_set_tuning", "gsl_lpa", "gsl_split",
                      "gsl_ctx_set_profiling", "gsl_ctx_get_profile",
-                     "gsl_modularity", "gsl_gsllpa", "gsl_gsllpa_host", "gsl_gsllpa_batch"):
+                     "gsl_modularity", "gsl_gsllpa", "gsl_gsllpa_host", "gsl_gsllpa_batch", "gsl_ctx_set_batch_mode",
+                     "gsl_server_create", "gsl_server_capacity", "gsl_server_submit", "gsl_server_wait",
+                     "gsl_server_get_stats", "gsl_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -172,6 +198,9 @@ class Context:
 
     def set_tuning(self, warp_max: int, blk_max: int):
         self._raise(self._lib.gsl_ctx_set_tuning(self._h, warp_max, blk_max))
+
+    def set_batch_mode(self, use_cuda_graph: bool):
+        self._raise(self._lib.gsl_ctx_set_batch_mode(self._h, int(bool(use_cuda_graph))))
 
     def set_profiling(self, enable: bool):
         """Enables (and zeroes) or disables per-slot CUDA-event profiling."""
@@ -272,6 +301,80 @@ class Context:
                                        _stream(stream))
         self._raise(rc)
         return (out, st.as_dict()) if stats else out
+
+
+class Server:
+    """Continuous-batching request server (see gsl_server_* in include/gsllpa.h).
+    Graphs are host arrays (numpy int64 offsets, int32 cols) that must stay
+    alive until their wait() returns; the server keeps a reference."""
+
+    def __init__(self, device=0, slots=2, slot_vertices=0, slot_entries=0, memory_fraction=0.5,
+                 max_batch_graphs=0, tolerance=0.05, max_iters=20, mode=MODE_SYNC):
+        import threading as _th
+        self._lib = load()
+        cfg = ServerConfig(device=device, slots=slots, slot_vertices=slot_vertices, slot_entries=slot_entries,
+                           memory_fraction=memory_fraction, max_batch_graphs=max_batch_graphs, mode=mode,
+                           tolerance=tolerance, max_iters=max_iters)
+        self._h = ctypes.c_void_p()
+        rc = self._lib.gsl_server_create(ctypes.byref(self._h), ctypes.byref(cfg))
+        if rc != 0:
+            raise GslError(rc, self._lib.gsl_strerror(rc).decode())
+        self._keep = {}
+        self._keep_lock = _th.Lock()
+
+    def capacity(self):
+        v, e = ctypes.c_int64(), ctypes.c_int64()
+        self._lib.gsl_server_capacity(self._h, ctypes.byref(v), ctypes.byref(e))
+        return v.value, e.value
+
+    def submit(self, offsets, cols):
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        col = np.ascontiguousarray(cols, dtype=np.int32)
+        rid = ctypes.c_int64()
+        rc = self._lib.gsl_server_submit(self._h, off.shape[0] - 1, col.shape[0], off.ctypes.data_as(ctypes.c_void_p),
+                                         col.ctypes.data_as(ctypes.c_void_p) if col.shape[0] else None,
+                                         ctypes.byref(rid))
+        if rc != 0:
+            raise GslError(rc, self._lib.gsl_strerror(rc).decode())
+        with self._keep_lock:
+            self._keep[rid.value] = (off, col)
+        return rid.value
+
+    def wait(self, rid, info=False):
+        import numpy as np
+        with self._keep_lock:
+            off, _ = self._keep[rid]
+        n = off.shape[0] - 1
+        out = np.empty(max(n, 1), dtype=np.int32)
+        ri = RequestInfo()
+        rc = self._lib.gsl_server_wait(self._h, rid, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ri))
+        with self._keep_lock:
+            self._keep.pop(rid, None)
+        if rc != 0:
+            raise GslError(rc, self._lib.gsl_strerror(rc).decode())
+        lab = out[:n]
+        if info:
+            return lab, {"sweeps": ri.sweeps, "batch_graphs": ri.batch_graphs, "queue_ms": ri.queue_ms,
+                         "service_ms": ri.service_ms, "latency_ms": ri.latency_ms}
+        return lab
+
+    def stats(self):
+        st = ServerStats()
+        self._lib.gsl_server_get_stats(self._h, ctypes.byref(st))
+        return {"completed": st.completed, "batches": st.batches, "queued": st.queued,
+                "max_concurrent_batches": st.max_concurrent_batches}
+
+    def close(self):
+        if self._h:
+            self._lib.gsl_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 -- interpreter shutdown
+            pass
 
 
 _default = {}

@@ -77,6 +77,7 @@ struct gsl_ctx {
   long long cap_lab_tmp = 0;
   cudaStream_t cap_stream = nullptr;   // captures and replays the batched sweep loop
   cudaGraphExec_t batch_exec = nullptr;
+  bool batch_direct = false;           // launch the batched loop directly instead of as a CUDA graph
   std::vector<long long> batch_key;    // arguments the captured graph was built for
 
   // profiling (gsl_ctx_set_profiling): CUDA-event time per launch sequence
@@ -464,6 +465,56 @@ int check_lpa_args(gsl_ctx* c, const gsl_csr* g, double tol, int32_t max_iters, 
   return GSL_OK;
 }
 
+// Enqueues the batched sweep loop (max_iters sweeps, unrolled, each
+// returning at once after every graph has stopped) and the final label
+// gather on stream cs, without synchronising: used under stream capture and
+// for direct launches.  prepare_graph, the vptr/gid upload and the per-graph
+// state reset must have been enqueued before.
+cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, const int32_t* weights, double tol,
+                                 int max_iters, bool async_mode, cudaStream_t cs) {
+  const long long n = g->n;
+  cudaError_t cerr = cudaSuccess;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && cerr == cudaSuccess) cerr = e;
+  };
+  ck(cudaMemsetAsync(c->flag[0], 0, (size_t)n, cs));
+  ck(cudaMemsetAsync(c->flag[1], 0, (size_t)n, cs));
+  ck(launch_init_labels(nullptr, c->lab[0], async_mode ? nullptr : c->lab[1], n, c->ctr, c->di, cs));
+  SweepArgs a{};
+  a.off = OFF(g);
+  a.col = g->cols;
+  a.w = weights;
+  a.ctr = c->ctr;
+  a.work = c->work;
+  a.wtab = c->wtab;
+  a.wtab_region = 2ll * c->tune.warp_max;
+  a.btab = c->btab;
+  a.btab_region = 2ll * c->ctr_h->max_degree;
+  a.n = n;
+  a.gid = c->gid;
+  a.vptr = c->vptr;
+  a.dn_graph = c->dn_graph;
+  a.stop = c->stop;
+  for (int t = 1; t <= max_iters; ++t) {
+    ck(cudaMemsetAsync(c->ctr, 0, offsetof(Counters, err), cs));
+    ck(cudaMemsetAsync(c->dn_graph, 0, sizeof(unsigned) * (size_t)num_graphs, cs));
+    ck(launch_bin(OFF(g), n, c->flag[t & 1], t <= 2 ? 1 : 0, c->tune, c->work, c->ctr, c->di, cs, c->gid,
+                  c->done, c->stop));
+    a.prev = async_mode ? c->lab[0] : c->lab[(t - 1) & 1];
+    a.next = async_mode ? c->lab[0] : c->lab[t & 1];
+    a.fnext = c->flag[(t + 1) & 1];
+    a.ident = (!async_mode && t == 1) ? 1 : 0;
+    a.check = t == 1 ? 1 : 0;
+    a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
+    a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
+    for (int k = 0; k < NCLASS; ++k) ck(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, cs));
+    ck(launch_graph_update(t, tol, max_iters, c->vptr, num_graphs, c->dn_graph, c->iters, c->done, c->stop, cs));
+  }
+  const int* bufs[2] = {c->lab[0], c->lab[1]};
+  ck(launch_batch_final(bufs, c->iters, c->gid, n, async_mode ? 1 : 0, c->lab_tmp, c->di, cs));
+  return cerr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -543,6 +594,12 @@ int gsl_ctx_set_tuning(gsl_ctx* c, int32_t warp_max, int32_t blk_max) {
     return fail(c, GSL_ERR_INVALID, "need 32 <= warp_max <= 2^20 and blk_max >= warp_max");
   c->tune.warp_max = warp_max;
   c->tune.blk_max = blk_max;
+  return GSL_OK;
+}
+
+int gsl_ctx_set_batch_mode(gsl_ctx* c, int32_t use_cuda_graph) {
+  if (!c) return GSL_ERR_INVALID;
+  c->batch_direct = use_cuda_graph == 0;
   return GSL_OK;
 }
 
@@ -694,50 +751,18 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
                                       (long long)c->lab[0], (long long)c->wtab, (long long)c->btab};
   long long graph_launches = 0;
   if (n > 0) {
-    if (!c->batch_exec || c->batch_key != key) {
+    if (c->batch_direct) {
+      const cudaError_t e = enqueue_batch_sweeps(c, g, num_graphs, weights, tol, max_iters, async_mode, s);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GSL_ERR_CUDA, "batched sweep loop: %s", cudaGetErrorString(e));
+      }
+    } else if (!c->batch_exec || c->batch_key != key) {
       if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
       c->batch_exec = nullptr;
       cudaStream_t cs = c->cap_stream;
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      cudaError_t cerr = cudaSuccess;
-      auto ck = [&](cudaError_t e) {
-        if (e != cudaSuccess && cerr == cudaSuccess) cerr = e;
-      };
-      ck(cudaMemsetAsync(c->flag[0], 0, (size_t)n, cs));
-      ck(cudaMemsetAsync(c->flag[1], 0, (size_t)n, cs));
-      ck(launch_init_labels(nullptr, c->lab[0], async_mode ? nullptr : c->lab[1], n, c->ctr, c->di, cs));
-      SweepArgs a{};
-      a.off = OFF(g);
-      a.col = g->cols;
-      a.w = weights;
-      a.ctr = c->ctr;
-      a.work = c->work;
-      a.wtab = c->wtab;
-      a.wtab_region = 2ll * c->tune.warp_max;
-      a.btab = c->btab;
-      a.btab_region = 2ll * c->ctr_h->max_degree;
-      a.n = n;
-      a.gid = c->gid;
-      a.vptr = c->vptr;
-      a.dn_graph = c->dn_graph;
-      a.stop = c->stop;
-      for (int t = 1; t <= max_iters; ++t) {
-        ck(cudaMemsetAsync(c->ctr, 0, offsetof(Counters, err), cs));
-        ck(cudaMemsetAsync(c->dn_graph, 0, sizeof(unsigned) * (size_t)num_graphs, cs));
-        ck(launch_bin(OFF(g), n, c->flag[t & 1], t <= 2 ? 1 : 0, c->tune, c->work, c->ctr, c->di, cs, c->gid,
-                      c->done, c->stop));
-        a.prev = async_mode ? c->lab[0] : c->lab[(t - 1) & 1];
-        a.next = async_mode ? c->lab[0] : c->lab[t & 1];
-        a.fnext = c->flag[(t + 1) & 1];
-        a.ident = (!async_mode && t == 1) ? 1 : 0;
-        a.check = t == 1 ? 1 : 0;
-        a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
-        a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
-        for (int k = 0; k < NCLASS; ++k) ck(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, cs));
-        ck(launch_graph_update(t, tol, max_iters, c->vptr, num_graphs, c->dn_graph, c->iters, c->done, c->stop, cs));
-      }
-      const int* bufs[2] = {c->lab[0], c->lab[1]};
-      ck(launch_batch_final(bufs, c->iters, c->gid, n, async_mode ? 1 : 0, c->lab_tmp, c->di, cs));
+      const cudaError_t cerr = enqueue_batch_sweeps(c, g, num_graphs, weights, tol, max_iters, async_mode, cs);
       cudaGraph_t graph = nullptr;
       const cudaError_t e_end = cudaStreamEndCapture(cs, &graph);
       if (cerr != cudaSuccess || e_end != cudaSuccess) {
@@ -755,12 +780,14 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
       }
       c->batch_key = key;
     }
-    CK(cudaEventRecord(c->ev[3], s));
-    CK(cudaStreamWaitEvent(c->cap_stream, c->ev[3], 0));
-    CK(cudaGraphLaunch(c->batch_exec, c->cap_stream));
-    graph_launches = 1;
-    CK(cudaEventRecord(c->ev[3], c->cap_stream));
-    CK(cudaStreamWaitEvent(s, c->ev[3], 0));
+    if (!c->batch_direct) {
+      CK(cudaEventRecord(c->ev[3], s));
+      CK(cudaStreamWaitEvent(c->cap_stream, c->ev[3], 0));
+      CK(cudaGraphLaunch(c->batch_exec, c->cap_stream));
+      graph_launches = 1;
+      CK(cudaEventRecord(c->ev[3], c->cap_stream));
+      CK(cudaStreamWaitEvent(s, c->ev[3], 0));
+    }
     CK(cudaEventRecord(c->ev[1], s));
     long long k = 0;
     if (int r = run_split(c, g, c->lab_tmp, labels_out, 0, &k, s)) return r;

@@ -382,104 +382,44 @@ __device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned c
   return 0;
 }
 
-// Inserts one 128-entry round -- four 32-entry chunks of labels l[u] and
-// weights w[u] -- into `tab`.  Equal labels within a chunk are merged with
-// __match_any_sync; when the round has at most 32 distinct (chunk, label)
-// pairs, the pairs of all four chunks are compacted into one warp (through
-// the warp's 32-slot `stage`) and merged again, so that each distinct label
-// of the round costs one table update.  Returns the slots created
-// (warp-uniform).
-template <bool WEIGHTED, bool GLOBAL>
-__device__ __forceinline__ unsigned insert_round(unsigned long long* tab, unsigned cap, const int (&l)[4],
-                                                 const int (&w)[4], int nchunks, unsigned long long* stage,
-                                                 unsigned long long& best, int* err) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
-  unsigned lead[4], cnt[4];
-  unsigned total = 0;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    lead[u] = 0;
-    cnt[u] = 0;
-    if (u < nchunks) {
-      const unsigned m = __match_any_sync(FULL, l[u]);
-      cnt[u] = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
-      lead[u] = __ballot_sync(FULL, l[u] >= 0 && (m & lt) == 0);
-      total += __popc(lead[u]);
-    }
-  }
-  unsigned made = 0;
-  if (total <= 32) {
-    unsigned base = 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if ((lead[u] >> lane) & 1u) stage[base + __popc(lead[u] & lt)] = ((unsigned long long)(unsigned)l[u] << 32) | cnt[u];
-      base += __popc(lead[u]);
-    }
-    __syncwarp();
-    const bool has = lane < (int)total;
-    const unsigned long long pr = has ? stage[lane] : 0ull;
-    __syncwarp();
-    const int ml = has ? (int)(pr >> 32) : -1;
-    const unsigned m2 = __match_any_sync(FULL, ml);
-    const unsigned c2 = __reduce_add_sync(m2, (unsigned)pr);
-    bool created = false;
-    if (has && (m2 & lt) == 0) {
-      const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)ml, c2, created, err);
-      const unsigned long long k = pack_key(sum, ml);
-      best = k > best ? k : best;
-    }
-    made = __popc(__ballot_sync(FULL, created));
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      bool created = false;
-      if ((lead[u] >> lane) & 1u) {
-        const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], cnt[u], created, err);
-        const unsigned long long k = pack_key(sum, l[u]);
-        best = k > best ? k : best;
-      }
-      made += __popc(__ballot_sync(FULL, created));
-    }
-  }
-  return made;
-}
-
-// Loads one 128-entry round of row (cp, wp, d) starting at e0: columns and
-// weights of four chunks first, then their labels, so that each lane has
-// eight loads in flight.
-template <bool WEIGHTED, bool ASYNC>
-__device__ __forceinline__ void load_round(const SweepArgs& a, int v, const int* cp, const int* wp, int d, int e0,
-                                           const Pol& pol, int (&l)[4], int (&w)[4], unsigned long long& wsum) {
-  const int lane = threadIdx.x & 31;
-  int j[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    check_same_graph(a, v, j[u]);
-    if (j[u] >= 0) wsum += (unsigned long long)w[u];
-    l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
-  }
-}
-
 // One warp aggregates the row (cp, wp, d) of vertex v into `tab` (cap
-// slots).  Returns true (warp-uniform) once more than `limit` distinct
-// labels have been inserted: the table is then abandoned.
+// slots).  Four 32-entry chunks are loaded (columns, then labels) before any
+// is hashed, so each lane keeps eight loads in flight.  Within a chunk equal
+// labels are merged with __match_any_sync and only the lowest lane of each
+// group inserts.  Returns true (warp-uniform) once more than `limit`
+// distinct labels have been inserted: the table is then abandoned.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
-                                         unsigned long long* stage, unsigned long long& best,
-                                         unsigned long long& wsum) {
+                                         unsigned long long& best, unsigned long long& wsum) {
   const int lane = threadIdx.x & 31;
   for (unsigned k = lane; k < cap; k += 32) tab[k] = EMPTY64;
   __syncwarp();
   unsigned used = 0;
   for (int e0 = 0; e0 < d; e0 += 128) {
-    int l[4], w[4];
-    load_round<WEIGHTED, ASYNC>(a, v, cp, wp, d, e0, pol, l, w, wsum);
-    const int nchunks = (d - e0 + 31) >> 5;
-    used += insert_round<WEIGHTED, GLOBAL>(tab, cap, l, w, nchunks, stage, best, &a.ctr->err);
+    int j[4], w[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      check_same_graph(a, v, j[u]);
+      if (j[u] >= 0) wsum += (unsigned long long)w[u];
+      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
+        const unsigned m = __match_any_sync(FULL, l[u]);
+        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+        bool created = false;
+        if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+          const unsigned long long k = pack_key(sum, l[u]);
+          best = k > best ? k : best;
+        }
+        if (limit != 0xFFFFFFFFu) used += __popc(__ballot_sync(FULL, created));
+      }
+    }
     if (used > limit) return true;   // at most 128 slots past the limit
   }
   return false;
@@ -494,8 +434,6 @@ template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL>
 __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_w64[];
-  __shared__ unsigned long long s_stage[8][32];
-  unsigned long long* stage = s_stage[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   unsigned long long* tab = smem_w64 + (size_t)(threadIdx.x >> 5) * TW;
   const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -535,10 +473,10 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
       const unsigned want = 2u * (unsigned)d;
       const unsigned cap = want < (unsigned)TW ? want : (unsigned)TW;
       const unsigned limit = (!SPILL || cap >= want) ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
-      if (warp_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, tab, cap, limit, pol, stage, best, wsum) && SPILL) {
+      if (warp_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, tab, cap, limit, pol, best, wsum) && SPILL) {
         best = 0;
         wsum = 0;
-        warp_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, stage, best, wsum);
+        warp_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum);
       }
       __syncwarp();
     }
@@ -568,15 +506,14 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
 }
 
 // One block aggregates the row of v into `tab`; every warp takes 128-entry
-// rounds.  Before each round a warp checks the block's overflow flag, and
-// after it adds its new slots to the block's count; past `limit` the flag is
-// raised (each of the block's warps may add one more round, at most 128
-// slots, before it sees the flag).  Returns the flag (block-uniform).
+// chunks.  Before each chunk a warp checks the block's overflow flag, and
+// after it adds its new slots to the block's count; past `limit` the flag
+// is raised.  Returns the flag (block-uniform after the barrier).
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
-                                         unsigned long long* stage, unsigned long long& best,
-                                         unsigned long long& wsum, unsigned* s_used, volatile int* s_ovf) {
+                                         unsigned long long& best, unsigned long long& wsum, unsigned* s_used,
+                                         volatile int* s_ovf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
   if (threadIdx.x == 0) {
@@ -585,12 +522,38 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* c
   }
   __syncthreads();
   for (int e0 = wid * 128; e0 < d; e0 += nw * 128) {
-    if (limit != 0xFFFFFFFFu && __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0)) break;
-    int l[4], w[4];
-    load_round<WEIGHTED, ASYNC>(a, v, cp, wp, d, e0, pol, l, w, wsum);
-    const int nchunks = (d - e0 + 31) >> 5;
-    const unsigned made = insert_round<WEIGHTED, GLOBAL>(tab, cap, l, w, nchunks, stage, best, &a.ctr->err);
-    if (limit != 0xFFFFFFFFu && lane == 0 && made && atomicAdd(s_used, made) + made > limit) *s_ovf = 1;
+    int j[4], w[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      check_same_graph(a, v, j[u]);
+      if (j[u] >= 0) wsum += (unsigned long long)w[u];
+      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
+    }
+    bool stop = false;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!stop && e0 + 32 * u < d) {
+        if (limit != 0xFFFFFFFFu && __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0)) {
+          stop = true;
+        } else {
+          const unsigned m = __match_any_sync(FULL, l[u]);
+          const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+          bool created = false;
+          if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+            const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+            const unsigned long long k = pack_key(sum, l[u]);
+            best = k > best ? k : best;
+          }
+          if (limit != 0xFFFFFFFFu) {
+            const unsigned nc = __popc(__ballot_sync(FULL, created));
+            if (lane == 0 && nc && atomicAdd(s_used, nc) + nc > limit) *s_ovf = 1;
+          }
+        }
+      }
+    }
+    if (stop) break;
   }
   __syncthreads();
   return *s_ovf;
@@ -604,8 +567,6 @@ template <bool WEIGHTED, bool ASYNC>
 __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, unsigned tb, int gthresh) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_b64[];
-  __shared__ unsigned long long s_stage[16][32];
-  unsigned long long* stage = s_stage[threadIdx.x >> 5];
   __shared__ unsigned long long s_best, s_wsum;
   __shared__ unsigned s_used;
   __shared__ int s_ovf, s_changed;
@@ -636,17 +597,15 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
       int ovf = 1;
       if (!(gthresh > 0 && d > gthresh)) {
         const unsigned cap = want < tb ? want : tb;
-        // up to 16 warps x 128 new slots may land after the flag is raised;
-        // a half-full table keeps linear probes short
-        const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 2;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, smem_b64, cap, limit, pol, stage, best, wsum,
-                                                &s_used, &s_ovf);
+        // each of up to 16 warps may add 32 new slots after the flag is raised
+        const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, smem_b64, cap, limit, pol, best, wsum, &s_used,
+                                                &s_ovf);
       }
       if (ovf) {
         best = 0;
         wsum = 0;
-        block_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, stage, best, wsum, &s_used,
-                                         &s_ovf);
+        block_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, &s_used, &s_ovf);
       }
     }
     best = warp_max_u64(best);
