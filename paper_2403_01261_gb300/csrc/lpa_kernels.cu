@@ -389,17 +389,26 @@ __device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned c
 // group inserts.  Returns true (warp-uniform) once more than `limit`
 // distinct labels have been inserted: the table is then abandoned.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
-__device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
+__device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
-                                         unsigned long long& best, unsigned long long& wsum) {
+                                         unsigned long long& best, unsigned long long& wsum, unsigned& own_sum) {
   const int lane = threadIdx.x & 31;
+  // columns of the first round are requested before the table is cleared
+  int jn[4], wn[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, 32 * u + lane, pol, jn[u], wn[u]);
   for (unsigned k = lane; k < cap; k += 32) tab[k] = EMPTY64;
   __syncwarp();
   unsigned used = 0;
   for (int e0 = 0; e0 < d; e0 += 128) {
     int j[4], w[4], l[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
+    for (int u = 0; u < 4; ++u) {
+      j[u] = jn[u];
+      w[u] = wn[u];
+    }
+    // labels of this round, then the columns of the next round, are in flight
+    // while this round is hashed
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       check_same_graph(a, v, j[u]);
@@ -407,8 +416,16 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, const int* c
       l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
     }
 #pragma unroll
+    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 128 + 32 * u + lane, pol, jn[u], wn[u]);
+#pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
+        // entries carrying the vertex's own label are summed in registers
+        const bool mine = l[u] == own;
+        own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
+                            : (unsigned)__popc(__ballot_sync(FULL, mine));
+        if (mine) l[u] = -1;
+        if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
         const unsigned m = __match_any_sync(FULL, l[u]);
         const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
         bool created = false;
@@ -431,7 +448,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, const int* c
 // without it the class bound guarantees 2 d <= TW.  The next vertex's
 // worklist entry and offsets are loaded while the current one is processed.
 template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL>
-__global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
+__global__ void __launch_bounds__(256, 3) sweep_warp_kernel(SweepArgs a, int cls) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_w64[];
   const int lane = threadIdx.x & 31;
@@ -473,12 +490,18 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
       const unsigned want = 2u * (unsigned)d;
       const unsigned cap = want < (unsigned)TW ? want : (unsigned)TW;
       const unsigned limit = (!SPILL || cap >= want) ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
-      if (warp_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, tab, cap, limit, pol, best, wsum) && SPILL) {
+      unsigned own_sum = 0;
+      if (warp_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, d, tab, cap, limit, pol, best, wsum, own_sum) && SPILL) {
         best = 0;
         wsum = 0;
-        warp_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum);
+        own_sum = 0;
+        warp_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, own_sum);
       }
       __syncwarp();
+      if (own_sum) {   // own_sum is warp-uniform
+        const unsigned long long k = pack_key(own_sum, old);
+        best = k > best ? k : best;
+      }
     }
     best = warp_max_u64(best);
     if (WEIGHTED && a.check) {
@@ -510,11 +533,14 @@ __global__ void __launch_bounds__(256) sweep_warp_kernel(SweepArgs a, int cls) {
 // after it adds its new slots to the block's count; past `limit` the flag
 // is raised.  Returns the flag (block-uniform after the barrier).
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
-__device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* cp, const int* wp, int d,
+__device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
-                                         unsigned long long& best, unsigned long long& wsum, unsigned* s_used,
-                                         volatile int* s_ovf) {
+                                         unsigned long long& best, unsigned long long& wsum, unsigned& own_sum,
+                                         unsigned* s_used, volatile int* s_ovf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int jn[4], wn[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, wid * 128 + 32 * u + lane, pol, jn[u], wn[u]);
   for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
   if (threadIdx.x == 0) {
     *s_used = 0;
@@ -524,13 +550,19 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* c
   for (int e0 = wid * 128; e0 < d; e0 += nw * 128) {
     int j[4], w[4], l[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 32 * u + lane, pol, j[u], w[u]);
+    for (int u = 0; u < 4; ++u) {
+      j[u] = jn[u];
+      w[u] = wn[u];
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       check_same_graph(a, v, j[u]);
       if (j[u] >= 0) wsum += (unsigned long long)w[u];
       l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      load_entry<WEIGHTED>(a, cp, wp, d, e0 + nw * 128 + 32 * u + lane, pol, jn[u], wn[u]);
     bool stop = false;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -538,6 +570,11 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* c
         if (limit != 0xFFFFFFFFu && __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0)) {
           stop = true;
         } else {
+          const bool mine = l[u] == own;
+          own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
+                              : (unsigned)__popc(__ballot_sync(FULL, mine));
+          if (mine) l[u] = -1;
+          if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
           const unsigned m = __match_any_sync(FULL, l[u]);
           const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
           bool created = false;
@@ -564,11 +601,11 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, const int* c
 // exceeds gthresh) is aggregated in the block's region of the global
 // fallback tables instead (a.btab_region slots).
 template <bool WEIGHTED, bool ASYNC>
-__global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, unsigned tb, int gthresh) {
+__global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cls, unsigned tb, int gthresh) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_b64[];
   __shared__ unsigned long long s_best, s_wsum;
-  __shared__ unsigned s_used;
+  __shared__ unsigned s_used, s_own;
   __shared__ int s_ovf, s_changed;
   unsigned long long* gtab = a.btab + (long long)blockIdx.x * a.btab_region;
   const unsigned cnt = a.ctr->cls_count[cls];
@@ -582,10 +619,13 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
     const int d = (int)(a.off[v + 1] - s);
     const int* cp = a.col + s;
     const int* wp = a.w + s;
+    const int old = own_label<ASYNC>(a, v);
     unsigned long long best = 0, wsum = 0;
+    unsigned own_sum = 0;
     if (threadIdx.x == 0) {
       s_best = 0;
       s_wsum = 0;
+      s_own = 0;
     }
     int sorted = 0;
     if (a.ident && !ASYNC)
@@ -599,17 +639,20 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
         const unsigned cap = want < tb ? want : tb;
         // each of up to 16 warps may add 32 new slots after the flag is raised
         const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, cp, wp, d, smem_b64, cap, limit, pol, best, wsum, &s_used,
-                                                &s_ovf);
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, d, smem_b64, cap, limit, pol, best, wsum, own_sum,
+                                                &s_used, &s_ovf);
       }
       if (ovf) {
         best = 0;
         wsum = 0;
-        block_row<WEIGHTED, ASYNC, true>(a, v, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, &s_used, &s_ovf);
+        own_sum = 0;
+        block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, own_sum,
+                                         &s_used, &s_ovf);
       }
     }
     best = warp_max_u64(best);
     if (lane == 0 && best) atomicMax(&s_best, best);
+    if (lane == 0 && own_sum) atomicAdd(&s_own, own_sum);   // own_sum is warp-uniform
     if (WEIGHTED && a.check) {
       wsum = warp_sum_u64(wsum);
       if (lane == 0 && wsum) atomicAdd(&s_wsum, wsum);
@@ -617,8 +660,12 @@ __global__ void __launch_bounds__(512) sweep_block_kernel(SweepArgs a, int cls, 
     __syncthreads();
     if (threadIdx.x == 0) {
       if (WEIGHTED && a.check && s_wsum >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
-      const int old = own_label<ASYNC>(a, v);
-      const int nl = s_best ? (int)~(unsigned)s_best : old;
+      unsigned long long b = s_best;
+      if (s_own) {
+        const unsigned long long k = pack_key(s_own, old);
+        b = k > b ? k : b;
+      }
+      const int nl = b ? (int)~(unsigned)b : old;
       const bool changed = nl != old;
       store_label<ASYNC>(a, v, nl, changed);
       if (changed) count_graph_change(a, v);
