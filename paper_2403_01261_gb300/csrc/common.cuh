@@ -33,6 +33,7 @@ struct Counters {
   unsigned int cls_count[NCLASS];          // frontier vertices per class this sweep
   unsigned int pad0;
   unsigned long long cls_scanned[NCLASS];  // CSR entries read per class this sweep
+  unsigned long long fast_active;          // vertices settled by the streaming identity sweep
   int err;                      // ERRBIT_* (sticky for the call)
   int pad1;
   // per-graph data filled by the class histogram

@@ -36,6 +36,8 @@ struct gsl_ctx {
   unsigned long long* partials = nullptr;
   long long cap_partials = 0;
 
+  unsigned* rowbits = nullptr;          // row-start bitmap of the streaming identity sweep
+  long long cap_rowbits = 0;
   unsigned long long* wtab = nullptr;   // warp-kernel fallback tables
   long long cap_wtab = 0;
   unsigned long long* btab = nullptr;   // block-kernel fallback tables
@@ -182,12 +184,12 @@ int map_err(gsl_ctx* c, int bits, const char* where) {
 }
 
 // ------------------------------------------------------------- profiling
-enum Slot { SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + NCLASS, SL_COUNT, SL_MOD, SL_N };
+enum Slot { SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + NCLASS, SL_COUNT, SL_MOD, SL_IDENT, SL_N };
 const char* slot_name(int k) {
   static const char* names[SL_N] = {"classify", "init_labels", "bin_frontier", "sweep_deg1", "sweep_deg2",
                                     "sweep_deg3_4", "sweep_deg5_8", "sweep_deg9_16", "sweep_deg17_32",
                                     "sweep_warp_small", "sweep_warp_large", "sweep_block", "sweep_hub",
-                                    "split_unionfind", "split_count_renumber", "modularity"};
+                                    "split_unionfind", "split_count_renumber", "modularity", "sweep1_stream"};
   return names[k];
 }
 
@@ -291,7 +293,21 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
   while (t < max_iters) {
     ++t;
     if (int r = reset_sweep_counters(c, s)) return r;
-    const bool all_active = t == 1 || !marked_prev;
+    bool all_active = t == 1 || !marked_prev;
+    // Sweep 1 from the identity labels with unit weights streams the rows;
+    // only rows that are not strictly increasing (flagged in flag[1]) go
+    // through the binned hash kernels below.
+    const bool stream1 = t == 1 && !async_mode && !labels_init && !weights;
+    if (stream1) {
+      if (int r = grow(c, c->rowbits, c->cap_rowbits, (g->nnz >> 5) + 1)) return r;
+      const int pe = prof_begin(c, s);
+      CK(launch_ident_stream(OFF(g), n, g->cols, g->nnz, c->rowbits, c->flag[1], c->lab[1], c->ctr, c->di, s));
+      prof_end(c, pe, SL_IDENT, s, 3);
+      c->profile.slot[SL_IDENT].vertices += n;
+      c->profile.slot[SL_IDENT].entries += g->nnz;
+      c->profile.slot[SL_IDENT].bytes += 4.0 * (double)g->nnz + 16.0 * (double)n;
+      all_active = false;   // the bin pass below picks up the flagged rows only
+    }
     {
       const int pe = prof_begin(c, s);
       CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s));
@@ -305,7 +321,9 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
       a.next = c->lab[t & 1];
     }
     a.fnext = c->flag[(t + 1) & 1];
-    a.ident = (!async_mode && !labels_init && t == 1) ? 1 : 0;
+    // (rows left over by the streaming pass are not strictly increasing, so
+    // the sorted-row shortcut of the hash kernels would fail on them)
+    a.ident = (!async_mode && !labels_init && t == 1 && !stream1) ? 1 : 0;
     a.check = t == 1 ? 1 : 0;
     // the first sweep that gathers labels after the identity sweep sees
     // almost as many distinct labels as neighbours (about 0.3 d on R-MAT
@@ -347,7 +365,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     }
     if (int r = map_err(c, c->ctr_h->err, "lpa")) return r;
     const long long dn = (long long)c->ctr_h->dn;
-    long long act = 0;
+    long long act = (long long)c->ctr_h->fast_active;
     for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
     scanned += (long long)c->ctr_h->scanned;
     if (st && t <= GSL_STATS_SWEEPS) {
@@ -569,7 +587,7 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   if (!c) return GSL_OK;
   DeviceGuard dg(c->device);
   void* dptrs[] = {c->lab[0], c->lab[1], c->flag[0], c->flag[1], c->work, c->parent, c->rank, c->sigma,
-                   c->block_sums, c->partials, c->wtab, c->btab, c->ctr, c->sums, c->k_dev,
+                   c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->ctr, c->sums, c->k_dev,
                    c->st_off, c->st_col, c->st_w, c->st_lab};
   for (void* p : dptrs)
     if (p) cudaFree(p);

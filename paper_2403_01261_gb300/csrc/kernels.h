@@ -66,6 +66,11 @@ cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool 
                                const DeviceInfo& di, cudaStream_t s);
 void count_launches(long long k);   // process-wide tally of kernels this library launched
 long long launches_total();
+// Streaming sweep 1 (identity labels, unit weights): bits holds nnz/32+1
+// words of scratch; rows that are not strictly increasing are flagged in
+// `bad` (n bytes, zero on entry) and left for the hash kernels.
+cudaError_t launch_ident_stream(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
+                                unsigned char* bad, int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
 cudaError_t launch_init_labels(const int* init, int* a, int* b, long long n, Counters* ctr,
                                const DeviceInfo& di, cudaStream_t s);
 long long block_grid_size(const Tuning& t, const DeviceInfo& di);   // blocks of the class 8/9 kernel

@@ -393,30 +393,41 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
                                          unsigned long long& best, unsigned long long& wsum, unsigned& own_sum) {
   const int lane = threadIdx.x & 31;
-  // columns of the first round are requested before the table is cleared
-  int jn[4], wn[4];
+  // three rounds in flight: labels of round r+1 and columns of round r+2
+  // are requested before round r is hashed
+  int jn[4], wn[4], ln[4], lw[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, 32 * u + lane, pol, jn[u], wn[u]);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    check_same_graph(a, v, jn[u]);
+    if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
+    ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+    lw[u] = wn[u];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, 128 + 32 * u + lane, pol, jn[u], wn[u]);
   for (unsigned k = lane; k < cap; k += 32) tab[k] = EMPTY64;
   __syncwarp();
   unsigned used = 0;
   for (int e0 = 0; e0 < d; e0 += 128) {
-    int j[4], w[4], l[4];
+    int l[4], w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      j[u] = jn[u];
-      w[u] = wn[u];
+      l[u] = ln[u];
+      w[u] = lw[u];
     }
-    // labels of this round, then the columns of the next round, are in flight
-    // while this round is hashed
+    if (e0 + 128 < d) {   // warp-uniform
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      check_same_graph(a, v, j[u]);
-      if (j[u] >= 0) wsum += (unsigned long long)w[u];
-      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
+      for (int u = 0; u < 4; ++u) {
+        check_same_graph(a, v, jn[u]);
+        if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
+        ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+        lw[u] = wn[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 256 + 32 * u + lane, pol, jn[u], wn[u]);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 128 + 32 * u + lane, pol, jn[u], wn[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
@@ -538,31 +549,44 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
                                          unsigned long long& best, unsigned long long& wsum, unsigned& own_sum,
                                          unsigned* s_used, volatile int* s_ovf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int jn[4], wn[4];
+  const int step = nw * 128;
+  int jn[4], wn[4], ln[4], lw[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, wid * 128 + 32 * u + lane, pol, jn[u], wn[u]);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    check_same_graph(a, v, jn[u]);
+    if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
+    ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+    lw[u] = wn[u];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, wid * 128 + step + 32 * u + lane, pol, jn[u], wn[u]);
   for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
   if (threadIdx.x == 0) {
     *s_used = 0;
     *s_ovf = 0;
   }
   __syncthreads();
-  for (int e0 = wid * 128; e0 < d; e0 += nw * 128) {
-    int j[4], w[4], l[4];
+  for (int e0 = wid * 128; e0 < d; e0 += step) {
+    int l[4], w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      j[u] = jn[u];
-      w[u] = wn[u];
+      l[u] = ln[u];
+      w[u] = lw[u];
     }
+    if (e0 + step < d) {   // warp-uniform
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      check_same_graph(a, v, j[u]);
-      if (j[u] >= 0) wsum += (unsigned long long)w[u];
-      l[u] = (j[u] >= 0 && j[u] != v) ? gather_label<ASYNC>(a, j[u], pol) : -1;
+      for (int u = 0; u < 4; ++u) {
+        check_same_graph(a, v, jn[u]);
+        if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
+        ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+        lw[u] = wn[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        load_entry<WEIGHTED>(a, cp, wp, d, e0 + 2 * step + 32 * u + lane, pol, jn[u], wn[u]);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      load_entry<WEIGHTED>(a, cp, wp, d, e0 + nw * 128 + 32 * u + lane, pol, jn[u], wn[u]);
     bool stop = false;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -684,6 +708,104 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
     __syncthreads();
   }
   flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// ---------------------------------------------------------------------------
+// Sweep 1 from the identity labelling with unit weights, as three streaming
+// passes instead of per-vertex row scans.  When a row is strictly
+// increasing every neighbour label (its id) occurs once with weight 1, so
+// Eq. 2's argmax with smallest-label ties is the smallest neighbour other
+// than the vertex itself: the first entry of the row, or the second when
+// the first is a self-loop.
+//   1. rowstart_kernel: bit off[v] set for every non-empty row;
+//   2. sorted_check_kernel: edge-parallel, flags every row that is not
+//      strictly increasing and checks every column's range;
+//   3. ident_first_kernel: writes the label of every unflagged row.
+// Flagged rows keep their flag and are swept by the hash kernels.
+__global__ void rowstart_kernel(const long long* __restrict__ off, long long n, unsigned* __restrict__ bits) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const long long st = off[v];
+    if (off[v + 1] > st) atomicOr(bits + (st >> 5), 1u << (st & 31));
+  }
+}
+
+__device__ __forceinline__ long long row_of(const long long* off, long long n, long long e) {
+  long long lo = 0, hi = n;   // largest r with off[r] <= e
+  while (hi - lo > 1) {
+    const long long mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) sorted_check_kernel(const long long* __restrict__ off, long long n,
+                                                            const int* __restrict__ col, long long nnz,
+                                                            const unsigned* __restrict__ bits,
+                                                            unsigned char* __restrict__ bad, Counters* ctr) {
+  const unsigned long long pol = policy_evict_first();
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long e0 = warp * 128; e0 < nnz; e0 += nwarps * 128) {
+    int j[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long e = e0 + 32 * u + lane;
+      j[u] = e < nnz ? ld_stream(col + e, pol) : 0;
+    }
+    const int tail = (lane == 31 && e0 + 128 < nnz) ? ld_stream(col + e0 + 128, pol) : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long e = e0 + 32 * u + lane;
+      int nxt = __shfl_down_sync(FULL, j[u], 1);
+      const int head = u < 3 ? __shfl_sync(FULL, j[u < 3 ? u + 1 : u], 0) : tail;
+      if (lane == 31) nxt = head;
+      if (e < nnz) {
+        if ((unsigned)j[u] >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
+        const long long f = e + 1;
+        const bool row_continues = f < nnz && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0;
+        if (row_continues && !(j[u] < nxt)) bad[row_of(off, n, e)] = 1;
+      }
+    }
+  }
+}
+
+__global__ void ident_first_kernel(const long long* __restrict__ off, long long n, const int* __restrict__ col,
+                                   const unsigned char* __restrict__ bad, int* __restrict__ next, Counters* ctr) {
+  unsigned long long my_dn = 0, my_scan = 0, my_act = 0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const long long st = off[v], d = off[v + 1] - st;
+    if (bad[v]) continue;
+    my_act += 1;
+    if (d == 0) continue;   // keeps its own label, already in `next`
+    int nl = col[st];
+    if (nl == (int)v) nl = d > 1 ? col[st + 1] : (int)v;
+    if ((unsigned)nl >= (unsigned)n) nl = (int)v;   // out of range: reported by the check pass
+    next[v] = nl;
+    my_dn += nl != (int)v ? 1ull : 0ull;
+    my_scan += (unsigned long long)d;
+  }
+  my_dn = warp_sum_u64(my_dn);
+  my_scan = warp_sum_u64(my_scan);
+  my_act = warp_sum_u64(my_act);
+  if ((threadIdx.x & 31) == 0) {
+    if (my_dn) atomicAdd(&ctr->dn, my_dn);
+    if (my_scan) atomicAdd(&ctr->scanned, my_scan);
+    if (my_act) atomicAdd(&ctr->fast_active, my_act);
+  }
+}
+
+cudaError_t launch_ident_stream(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
+                                unsigned char* bad, int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int g = 8 * di.sm_count;
+  cudaMemsetAsync(bits, 0, sizeof(unsigned) * (size_t)((nnz >> 5) + 1), s);
+  rowstart_kernel<<<g, 256, 0, s>>>(off, n, bits);
+  if (nnz > 0) sorted_check_kernel<<<g, 256, 0, s>>>(off, n, col, nnz, bits, bad, ctr);
+  ident_first_kernel<<<g, 256, 0, s>>>(off, n, col, bad, next, ctr);
+  count_launches(nnz > 0 ? 3 : 2);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

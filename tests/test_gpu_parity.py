@@ -261,6 +261,43 @@ def test_duplicate_entries_unsorted_rows(ctx, small_ctx):
         assert np.array_equal(c.gsllpa(off, col).cpu().numpy(), O.gsl_lpa(h, 0.05, 20)[0])
 
 
+def _mixed_rows(seed=7):
+    """R-MAT rows of every kind the first sweep meets: strictly increasing,
+    a self-loop first or inside, a duplicated entry, shuffled."""
+    rng = np.random.default_rng(seed)
+    g = I.rmat(13, 16, seed=6)
+    src = np.repeat(np.arange(g.n), np.diff(g.offsets))
+    pairs = np.stack([src, g.cols], 1)
+    pairs = pairs[pairs[:, 0] < pairs[:, 1]]
+    dup = pairs[rng.random(len(pairs)) < 0.01]
+    loops = np.arange(g.n)[rng.random(g.n) < 0.1]
+    allp = np.concatenate([pairs, dup, pairs[:, ::-1], dup[:, ::-1], np.stack([loops, loops], 1)])
+    allp = allp[np.lexsort((allp[:, 1], allp[:, 0]))]
+    offsets = np.zeros(g.n + 1, dtype=np.int64)
+    np.add.at(offsets, allp[:, 0] + 1, 1)
+    offsets = np.cumsum(offsets)
+    cols = allp[:, 1].astype(np.int32)
+    for v in np.arange(g.n)[rng.random(g.n) < 0.05]:   # shuffle some rows
+        rng.shuffle(cols[offsets[v]:offsets[v + 1]])
+    return I.Graph(offsets, cols, name="rmat13-mixed-rows")
+
+
+def test_first_sweep_mixed_rows(ctx, small_ctx):
+    h = _mixed_rows()
+    d = np.diff(h.offsets)
+    assert d.max() > 512 and (d == 0).any()
+    off, col, _ = dev(h)
+    for c in (ctx, small_ctx):
+        for iters in (1, 2):
+            want, t, dn = O.lpa_sync(h, 0.0, iters)
+            got, st = c.lpa(off, col, tolerance=0.0, max_iters=iters, stats=True)
+            assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
+            assert st["active"][0] == h.n and st["edges_scanned"] >= h.nnz
+        got, st = c.lpa(off, col, stats=True)
+        want, t, dn = O.lpa_sync(h, 0.05, 20)
+        assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
+
+
 def test_invalid_inputs_are_rejected(ctx, gpu_lib):
     g = I.path(6)
     off, col, _ = dev(g)
