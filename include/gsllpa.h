@@ -92,6 +92,31 @@ int gsl_ctx_destroy(gsl_ctx* ctx);
  * warp_max <= blk_max.  Results do not depend on these values. */
 int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
 
+/* Result of gsl_autotune. */
+typedef struct {
+  int32_t warp_max;     /* chosen thresholds (now set on the context) */
+  int32_t blk_max;
+  int32_t candidates;   /* threshold pairs timed */
+  int32_t sweeps;       /* sweeps timed per pair */
+  float best_ms;        /* device time of those sweeps with the chosen pair */
+  float entry_ms;       /* and with the pair the context had on entry */
+} gsl_tune_result;
+
+/* Autotuner for the degree-class thresholds (the paper has no counterpart:
+ * its CPU design has no degree classes).  Runs the first `sweeps` sweeps
+ * of synchronous or asynchronous LPA (mode) from the identity labels on
+ * graph g (device CSR, weights as in gsl_lpa) once per candidate pair of
+ * warp_max in {128, 256, 512, 1024} and blk_max in {4096, 12288, 32768,
+ * 131072} with blk_max >= warp_max (pairs that bin g's vertices alike are
+ * timed once), each timed with CUDA events on `stream`, and sets the
+ * fastest pair on the context (the pair the context had on entry wins
+ * ties).  1 <= sweeps <= 64.  Labels do not depend on the thresholds, so
+ * tuning changes only speed.  The context's scratch is used; the graph
+ * is only read.  Synchronises `stream`.  Errors as gsl_lpa; on error the
+ * entry thresholds are restored. */
+int gsl_autotune(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, int32_t mode, int32_t sweeps,
+                 gsl_tune_result* out, void* stream);
+
 /* Label propagation: lpa() of Algorithm 3 without its final split (the
  * "GVE-LPA" phase).  Labels start as labels_init (device int32[n], values
  * in [0, n)) or, when labels_init is NULL, as C = [0 .. n).  Each sweep

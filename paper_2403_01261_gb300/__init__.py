@@ -71,6 +71,11 @@ class ServerStats(ctypes.Structure):
                 ("max_concurrent_batches", ctypes.c_int64)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("warp_max", ctypes.c_int32), ("blk_max", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("sweeps", ctypes.c_int32), ("best_ms", ctypes.c_float), ("entry_ms", ctypes.c_float)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("changed", ctypes.c_int64 * STATS_SWEEPS), ("active", ctypes.c_int64 * STATS_SWEEPS),
@@ -109,6 +114,7 @@ def load():
         lib.gsl_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
         lib.gsl_ctx_destroy.argtypes = [P]
         lib.gsl_ctx_set_tuning.argtypes = [P, i32, i32]
+        lib.gsl_autotune.argtypes = [P, cp, P, i32, i32, ctypes.POINTER(TuneResult), P]
         lib.gsl_lpa.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_split.argtypes = [P, cp, P, P, i32, ctypes.POINTER(i64), P]
         lib.gsl_modularity.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
@@ -198,6 +204,15 @@ class Context:
 
     def set_tuning(self, warp_max: int, blk_max: int):
         self._raise(self._lib.gsl_ctx_set_tuning(self._h, warp_max, blk_max))
+
+    def autotune(self, offsets, cols, weights=None, mode=MODE_SYNC, sweeps=4, stream=None):
+        """Times the first `sweeps` sweeps under each candidate threshold pair
+        and sets the fastest on this context; returns the choice and times."""
+        g = _check_graph(offsets, cols, weights)
+        r = TuneResult()
+        self._raise(self._lib.gsl_autotune(self._h, ctypes.byref(g), _ptr(weights), int(mode), int(sweeps),
+                                           ctypes.byref(r), _stream(stream)))
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def set_batch_mode(self, use_cuda_graph: bool):
         self._raise(self._lib.gsl_ctx_set_batch_mode(self._h, int(bool(use_cuda_graph))))

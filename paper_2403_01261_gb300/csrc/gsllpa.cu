@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/gsllpa.h"
@@ -615,6 +616,93 @@ int gsl_ctx_set_tuning(gsl_ctx* c, int32_t warp_max, int32_t blk_max) {
   return GSL_OK;
 }
 
+// Binning signature of a threshold pair on the current graph: two pairs
+// that put every vertex in the same class run the same kernels.
+namespace {
+bool same_binning(const std::vector<long long>& deg_sorted, const gsl::Tuning& a, const gsl::Tuning& b) {
+  auto count_le = [&](long long x) {
+    return (long long)(std::upper_bound(deg_sorted.begin(), deg_sorted.end(), x) - deg_sorted.begin());
+  };
+  const gsl::ClassBounds ca = gsl::class_bounds(a), cb = gsl::class_bounds(b);
+  return count_le(ca.warp_small) == count_le(cb.warp_small) && count_le(ca.warp_max) == count_le(cb.warp_max) &&
+         count_le(ca.blk_max) == count_le(cb.blk_max);
+}
+}  // namespace
+
+int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t mode, int32_t sweeps,
+                 gsl_tune_result* out, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (!out) return fail(c, GSL_ERR_INVALID, "out is NULL");
+  if (sweeps < 1 || sweeps > GSL_STATS_SWEEPS) return fail(c, GSL_ERR_INVALID, "need 1 <= sweeps <= 64");
+  if (int r = check_csr(c, g)) return r;
+  if (mode != GSL_MODE_SYNC && mode != GSL_MODE_ASYNC) return fail(c, GSL_ERR_INVALID, "unknown mode");
+  const Tuning entry = c->tune;
+  memset(out, 0, sizeof(*out));
+  out->warp_max = entry.warp_max;
+  out->blk_max = entry.blk_max;
+  out->sweeps = sweeps;
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  // sorted degrees (host copy of the offsets) decide which pairs bin alike
+  std::vector<long long> offs((size_t)g->n + 1);
+  CK(cudaMemcpyAsync(offs.data(), g->offsets, sizeof(int64_t) * offs.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<long long> deg((size_t)g->n);
+  for (long long v = 0; v < g->n; ++v) deg[(size_t)v] = offs[(size_t)v + 1] - offs[(size_t)v];
+  std::sort(deg.begin(), deg.end());
+  std::vector<Tuning> cand{entry};
+  for (int wm : {128, 256, 512, 1024})
+    for (int bm : {4096, 12288, 32768, 131072}) {
+      if (bm < wm) continue;
+      Tuning t = entry;
+      t.warp_max = wm;
+      t.blk_max = bm;
+      bool dup = false;
+      for (const Tuning& u : cand) dup = dup || same_binning(deg, t, u);
+      if (!dup) cand.push_back(t);
+    }
+  auto time_one = [&](const Tuning& t, float* ms) -> int {
+    c->tune = t;
+    if (int r = prepare_graph(c, g, s)) return r;
+    int* fin = nullptr;
+    CK(cudaEventRecord(c->ev[0], s));
+    if (int r = run_lpa(c, g, weights, nullptr, 0.0, sweeps, mode, nullptr, s, &fin)) return r;
+    CK(cudaEventRecord(c->ev[1], s));
+    CK(cudaEventSynchronize(c->ev[1]));
+    CK(cudaEventElapsedTime(ms, c->ev[0], c->ev[1]));
+    return GSL_OK;
+  };
+  float ms = 0.f;
+  int best = 0;
+  float best_ms = 0.f;
+  for (size_t k = 0; k < cand.size(); ++k) {
+    if (k == 0) {   // untimed warm-up run with the entry pair
+      if (int r = time_one(cand[0], &ms)) {
+        c->tune = entry;
+        return r;
+      }
+    }
+    if (int r = time_one(cand[k], &ms)) {
+      c->tune = entry;
+      return r;
+    }
+    if (k == 0) out->entry_ms = ms;
+    if (k == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = (int)k;
+    }
+  }
+  c->tune = cand[(size_t)best];
+  out->warp_max = c->tune.warp_max;
+  out->blk_max = c->tune.blk_max;
+  out->candidates = (int32_t)cand.size();
+  out->best_ms = best_ms;
+  return GSL_OK;
+}
+
 int gsl_ctx_set_batch_mode(gsl_ctx* c, int32_t use_cuda_graph) {
   if (!c) return GSL_ERR_INVALID;
   c->batch_direct = use_cuda_graph == 0;
@@ -766,7 +854,8 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
   // graph; sweeps after the last graph stops return at once.
   const std::vector<long long> key = {(long long)OFF(g), (long long)g->cols, (long long)weights, n, g->nnz,
                                       num_graphs, max_iters, mode, (long long)(tol * 1e12), c->ctr_h->max_degree,
-                                      (long long)c->lab[0], (long long)c->wtab, (long long)c->btab};
+                                      (long long)c->lab[0], (long long)c->wtab, (long long)c->btab,
+                                      c->tune.warp_max, c->tune.blk_max};
   long long graph_launches = 0;
   if (n > 0) {
     if (c->batch_direct) {

@@ -539,20 +539,52 @@ __global__ void __launch_bounds__(256, 3) sweep_warp_kernel(SweepArgs a, int cls
   flush_counters(a.ctr, cls, my_dn, my_scan);
 }
 
-// One block aggregates the row of v into `tab`; every warp takes 128-entry
-// chunks.  Before each chunk a warp checks the block's overflow flag, and
-// after it adds its new slots to the block's count; past `limit` the flag
-// is raised.  Returns the flag (block-uniform after the barrier).
+// Per-row values shared by a block.  Rows alternate between two copies, so
+// a row's copy can be reset while slower threads still read the previous
+// row's: the one before that is provably no longer read.
+struct BlockRowShared {
+  unsigned long long best[2], wsum[2];
+  unsigned used[2], own[2];
+  int ovf[2];
+};
+
+// Reduces the block's per-thread partial results into sh[par]; the caller
+// synchronises before reading them.
+template <bool WEIGHTED>
+__device__ __forceinline__ void block_publish(const SweepArgs& a, BlockRowShared& sh, int par,
+                                              unsigned long long best, unsigned long long wsum, unsigned own_sum) {
+  const int lane = threadIdx.x & 31;
+  best = warp_max_u64(best);
+  if (lane == 0 && best) atomicMax(&sh.best[par], best);
+  if (lane == 0 && own_sum) atomicAdd(&sh.own[par], own_sum);   // own_sum is warp-uniform
+  if (WEIGHTED && a.check) {
+    wsum = warp_sum_u64(wsum);
+    if (lane == 0 && wsum) atomicAdd(&sh.wsum[par], wsum);
+  }
+}
+
+// One block aggregates the row of v into `tab` and publishes the result in
+// sh[par].  A round covers blockDim.x * 4 entries; chunk u of warp w in the
+// round starting at r0 holds entries r0 + (u * warps + w) * 32 + lane, so a
+// row shorter than a round still spreads over every warp.  With a finite
+// `limit` (shared table), a warp checks the overflow flag before each chunk
+// and adds its new slots to the block's count after it; past `limit` the
+// flag is raised and the row is abandoned.  Returns the flag (block-uniform
+// after the closing barrier).  The global-table pass (limit infinite) leaves
+// the flag alone, so every thread still reads the value that sent it there.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
-                                         unsigned long long& best, unsigned long long& wsum, unsigned& own_sum,
-                                         unsigned* s_used, volatile int* s_ovf) {
+                                         BlockRowShared& sh, int par) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int step = nw * 128;
+  const int cb = wid * 32 + lane;   // offset of chunk 0 within a round
+  const int cu = nw * 32;           // distance between the chunks of a warp
+  unsigned long long best = 0, wsum = 0;
+  unsigned own_sum = 0;
   int jn[4], wn[4], ln[4], lw[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, wid * 128 + 32 * u + lane, pol, jn[u], wn[u]);
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, cb + u * cu, pol, jn[u], wn[u]);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     check_same_graph(a, v, jn[u]);
@@ -561,21 +593,26 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
     lw[u] = wn[u];
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, wid * 128 + step + 32 * u + lane, pol, jn[u], wn[u]);
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, step + cb + u * cu, pol, jn[u], wn[u]);
   for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
   if (threadIdx.x == 0) {
-    *s_used = 0;
-    *s_ovf = 0;
+    sh.best[par] = 0;
+    sh.wsum[par] = 0;
+    sh.own[par] = 0;
+    if (!GLOBAL) {
+      sh.used[par] = 0;
+      sh.ovf[par] = 0;
+    }
   }
   __syncthreads();
-  for (int e0 = wid * 128; e0 < d; e0 += step) {
+  for (int r0 = 0; r0 < d; r0 += step) {
     int l[4], w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       l[u] = ln[u];
       w[u] = lw[u];
     }
-    if (e0 + step < d) {   // warp-uniform
+    if (r0 + step < d) {   // block-uniform
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         check_same_graph(a, v, jn[u]);
@@ -584,14 +621,14 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
         lw[u] = wn[u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        load_entry<WEIGHTED>(a, cp, wp, d, e0 + 2 * step + 32 * u + lane, pol, jn[u], wn[u]);
+      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, r0 + 2 * step + cb + u * cu, pol, jn[u], wn[u]);
     }
     bool stop = false;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (!stop && e0 + 32 * u < d) {
-        if (limit != 0xFFFFFFFFu && __shfl_sync(FULL, lane == 0 ? *s_ovf : 0, 0)) {
+      if (!stop && r0 + (u * nw + wid) * 32 < d) {   // warp-uniform
+        if (!GLOBAL && limit != 0xFFFFFFFFu &&
+            __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sh.ovf[par] : 0, 0)) {
           stop = true;
         } else {
           const bool mine = l[u] == own;
@@ -607,105 +644,112 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
             const unsigned long long k = pack_key(sum, l[u]);
             best = k > best ? k : best;
           }
-          if (limit != 0xFFFFFFFFu) {
+          if (!GLOBAL && limit != 0xFFFFFFFFu) {
             const unsigned nc = __popc(__ballot_sync(FULL, created));
-            if (lane == 0 && nc && atomicAdd(s_used, nc) + nc > limit) *s_ovf = 1;
+            if (lane == 0 && nc && atomicAdd(&sh.used[par], nc) + nc > limit) *(volatile int*)&sh.ovf[par] = 1;
           }
         }
       }
     }
     if (stop) break;
   }
+  block_publish<WEIGHTED>(a, sh, par, best, wsum, own_sum);
   __syncthreads();
-  return *s_ovf;
+  return GLOBAL ? 0 : *(volatile int*)&sh.ovf[par];
 }
 
 // Classes 8 and 9: one block per vertex, `tb` slots of shared memory; a
 // vertex whose labels overflow it (or, when gthresh > 0, whose degree
 // exceeds gthresh) is aggregated in the block's region of the global
-// fallback tables instead (a.btab_region slots).
+// fallback tables instead (a.btab_region slots).  Two barriers per row: one
+// after the table is cleared, one after the partial results are published.
+// The worklist entry of the row after next and the offsets and own label
+// of the next row are loaded while the current row is processed.
 template <bool WEIGHTED, bool ASYNC>
 __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cls, unsigned tb, int gthresh) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_b64[];
-  __shared__ unsigned long long s_best, s_wsum;
-  __shared__ unsigned s_used, s_own;
-  __shared__ int s_ovf, s_changed;
+  __shared__ BlockRowShared sh;
   unsigned long long* gtab = a.btab + (long long)blockIdx.x * a.btab_region;
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
   const Pol pol = make_pol();
-  const int lane = threadIdx.x & 31;
+  const long long G = gridDim.x;
   unsigned long long my_dn = 0, my_scan = 0;
-  for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
-    const int v = work[item];
-    const long long s = a.off[v];
-    const int d = (int)(a.off[v + 1] - s);
+  long long item = blockIdx.x;
+  int v = 0, old = 0, v1 = 0;
+  long long s = 0, e = 0;
+  if (item < (long long)cnt) {
+    v = work[item];
+    s = a.off[v];
+    e = a.off[v + 1];
+    old = own_label<ASYNC>(a, v);
+  }
+  if (item + G < (long long)cnt) v1 = work[item + G];
+  for (int par = 0; item < (long long)cnt; item += G, par ^= 1) {
+    long long s1 = 0, e1 = 0;
+    int old1 = 0, v2 = 0;
+    if (item + G < (long long)cnt) {
+      s1 = a.off[v1];
+      e1 = a.off[v1 + 1];
+      old1 = own_label<ASYNC>(a, v1);
+    }
+    if (item + 2 * G < (long long)cnt) v2 = work[item + 2 * G];
+    const int d = (int)(e - s);
     const int* cp = a.col + s;
     const int* wp = a.w + s;
-    const int old = own_label<ASYNC>(a, v);
-    unsigned long long best = 0, wsum = 0;
-    unsigned own_sum = 0;
-    if (threadIdx.x == 0) {
-      s_best = 0;
-      s_wsum = 0;
-      s_own = 0;
-    }
     int sorted = 0;
-    if (a.ident && !ASYNC)
+    if (a.ident && !ASYNC) {
+      unsigned long long best = 0, wsum = 0;
+      if (threadIdx.x == 0) {
+        sh.best[par] = 0;
+        sh.wsum[par] = 0;
+        sh.own[par] = 0;
+      }
       sorted = __syncthreads_and(ident_sorted_pass<WEIGHTED>(a, v, s, d, threadIdx.x, blockDim.x, pol, best, wsum));
+      if (sorted) {
+        block_publish<WEIGHTED>(a, sh, par, best, wsum, 0u);
+        __syncthreads();
+      }
+    }
     if (!sorted) {
-      best = 0;
-      wsum = 0;
       const unsigned want = 2u * (unsigned)d;
       int ovf = 1;
       if (!(gthresh > 0 && d > gthresh)) {
         const unsigned cap = want < tb ? want : tb;
         // each of up to 16 warps may add 32 new slots after the flag is raised
         const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, d, smem_b64, cap, limit, pol, best, wsum, own_sum,
-                                                &s_used, &s_ovf);
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, d, smem_b64, cap, limit, pol, sh, par);
       }
-      if (ovf) {
-        best = 0;
-        wsum = 0;
-        own_sum = 0;
-        block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, own_sum,
-                                         &s_used, &s_ovf);
-      }
+      if (ovf) block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
     }
-    best = warp_max_u64(best);
-    if (lane == 0 && best) atomicMax(&s_best, best);
-    if (lane == 0 && own_sum) atomicAdd(&s_own, own_sum);   // own_sum is warp-uniform
-    if (WEIGHTED && a.check) {
-      wsum = warp_sum_u64(wsum);
-      if (lane == 0 && wsum) atomicAdd(&s_wsum, wsum);
+    unsigned long long b = sh.best[par];
+    const unsigned own_sum = sh.own[par];
+    if (own_sum) {
+      const unsigned long long k = pack_key(own_sum, old);
+      b = k > b ? k : b;
     }
-    __syncthreads();
+    const int nl = b ? (int)~(unsigned)b : old;
+    const bool changed = nl != old;
     if (threadIdx.x == 0) {
-      if (WEIGHTED && a.check && s_wsum >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
-      unsigned long long b = s_best;
-      if (s_own) {
-        const unsigned long long k = pack_key(s_own, old);
-        b = k > b ? k : b;
-      }
-      const int nl = b ? (int)~(unsigned)b : old;
-      const bool changed = nl != old;
+      if (WEIGHTED && a.check && sh.wsum[par] >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
       store_label<ASYNC>(a, v, nl, changed);
       if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;
       my_dn += changed ? 1ull : 0ull;
-      s_changed = changed;
     }
-    __syncthreads();
-    if (s_changed && a.mark) {
-      for (int e = threadIdx.x; e < d; e += blockDim.x) {
-        const int j = ld_stream(cp + e, pol.stream);
+    if (changed && a.mark) {   // block-uniform
+      for (int x = threadIdx.x; x < d; x += blockDim.x) {
+        const int j = ld_stream(cp + x, pol.stream);
         if ((unsigned)j < (unsigned)a.n) a.fnext[j] = 1;
       }
       if (!ASYNC && threadIdx.x == 0) a.fnext[v] = 1;
     }
-    __syncthreads();
+    v = v1;
+    s = s1;
+    e = e1;
+    old = old1;
+    v1 = v2;
   }
   flush_counters(a.ctr, cls, my_dn, my_scan);
 }
@@ -776,9 +820,8 @@ __global__ void ident_first_kernel(const long long* __restrict__ off, long long 
   unsigned long long my_dn = 0, my_scan = 0, my_act = 0;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
     const long long st = off[v], d = off[v + 1] - st;
-    if (bad[v]) continue;
+    if (d == 0 || bad[v]) continue;   // an empty row keeps its label, already in `next`
     my_act += 1;
-    if (d == 0) continue;   // keeps its own label, already in `next`
     int nl = col[st];
     if (nl == (int)v) nl = d > 1 ? col[st + 1] : (int)v;
     if ((unsigned)nl >= (unsigned)n) nl = (int)v;   // out of range: reported by the check pass

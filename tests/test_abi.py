@@ -38,6 +38,12 @@ def test_host_only_entry_points():
     h = ctypes.c_void_p()
     rc = lib.gsl_ctx_create(ctypes.byref(h), 10_000)
     assert rc != 0 and not h.value
+    # entry points taking a context reject NULL before touching a device
+    P = ctypes.c_void_p
+    lib.gsl_autotune.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, P, P]
+    assert lib.gsl_autotune(None, None, None, 0, 4, None, None) == 1
+    lib.gsl_ctx_set_tuning.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+    assert lib.gsl_ctx_set_tuning(None, 1024, 32768) == 1
 
 
 def test_product_path_does_not_touch_the_oracle():

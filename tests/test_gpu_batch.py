@@ -110,3 +110,19 @@ def test_batch_rejects_edges_between_graphs(ctx, gpu_lib):
         ctx.gsllpa_batch(torch.from_numpy(off).cuda(), torch.from_numpy(col).cuda(), vptr)
     with pytest.raises(gpu_lib.GslError):
         ctx.gsllpa_batch(torch.from_numpy(off).cuda(), torch.from_numpy(col).cuda(), np.array([0, 3, 2], np.int64))
+
+
+def test_batch_thresholds_changed_between_calls(gpu_lib):
+    """A new threshold pair on the same buffers re-captures the sweep loop."""
+    c = gpu_lib.Context(0)
+    graphs = mixed_graphs(10, seed=11)
+    off, col, w, vptr = pack(graphs)
+    t = lambda a: torch.from_numpy(a).cuda()
+    d_off, d_col = t(off), t(col)
+    wants = [O.gsl_lpa(g, 0.05, 20) for g in graphs]
+    for wm, bm in ((1024, 32768), (32, 40), (64, 4096), (1024, 32768)):
+        c.set_tuning(wm, bm)
+        labels, iters = c.gsllpa_batch(d_off, d_col, vptr)
+        labels = labels.cpu().numpy()
+        for k, (want, tt, _) in enumerate(wants):
+            assert iters[k] == tt and np.array_equal(labels[vptr[k]:vptr[k + 1]], want), (wm, bm, k)

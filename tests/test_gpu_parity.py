@@ -292,7 +292,7 @@ def test_first_sweep_mixed_rows(ctx, small_ctx):
             want, t, dn = O.lpa_sync(h, 0.0, iters)
             got, st = c.lpa(off, col, tolerance=0.0, max_iters=iters, stats=True)
             assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
-            assert st["active"][0] == h.n and st["edges_scanned"] >= h.nnz
+            assert st["active"][0] == (d > 0).sum() and st["edges_scanned"] >= h.nnz
         got, st = c.lpa(off, col, stats=True)
         want, t, dn = O.lpa_sync(h, 0.05, 20)
         assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
@@ -330,6 +330,21 @@ def test_invalid_inputs_are_rejected(ctx, gpu_lib):
         ctx.lpa(off, col, tolerance=-1.0)
     # the context stays usable after errors
     assert np.array_equal(ctx.gsllpa(off, col).cpu().numpy(), O.gsl_lpa(g, 0.05, 20)[0])
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(gpu_lib):
+    g = I.rmat(15, 16, seed=4)
+    off, col, _ = dev(g)
+    c = gpu_lib.Context(0)
+    r = c.autotune(off, col, sweeps=3)
+    assert r["candidates"] >= 2 and r["sweeps"] == 3
+    assert r["warp_max"] in (128, 256, 512, 1024) and r["blk_max"] in (4096, 12288, 32768, 131072)
+    assert 0 < r["best_ms"] <= r["entry_ms"]
+    want, t, dn = O.lpa_sync(g, 0.05, 20)
+    got, st = c.lpa(off, col, stats=True)
+    assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
+    with pytest.raises(gpu_lib.GslError):
+        c.autotune(off, col, sweeps=0)
 
 
 def test_tuning_does_not_change_results(gpu_lib):
