@@ -92,11 +92,24 @@ int gsl_ctx_destroy(gsl_ctx* ctx);
  * warp_max <= blk_max.  Results do not depend on these values. */
 int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
 
+/* Two-phase synchronous sweeps (the paper has no counterpart: it is a GPU
+ * scheduling choice).  In a two-phase sweep one edge-parallel pass first
+ * gathers the label of every CSR entry's neighbour into a context-owned
+ * int32[nnz] array, and the per-vertex kernels then read those labels
+ * sequentially instead of gathering them.  mode 0: never; 1:
+ * when the graph has at least 2^22 entries and the sweep runs on all
+ * vertices or the previous sweep changed more than a quarter of them;
+ * 2: every synchronous sweep that reads labels (not sweep 1 from the
+ * identity labelling).  Default 0; gsl_autotune may choose 1.  Labels and
+ * statistics do not depend on the mode. */
+int gsl_ctx_set_pregather(gsl_ctx* ctx, int32_t mode);
+
 /* Result of gsl_autotune. */
 typedef struct {
   int32_t warp_max;     /* chosen thresholds (now set on the context) */
   int32_t blk_max;
-  int32_t candidates;   /* threshold pairs timed */
+  int32_t pregather;    /* chosen two-phase mode (gsl_ctx_set_pregather) */
+  int32_t candidates;   /* settings timed */
   int32_t sweeps;       /* sweeps timed per pair */
   float best_ms;        /* device time of those sweeps with the chosen pair */
   float entry_ms;       /* and with the pair the context had on entry */
@@ -105,12 +118,12 @@ typedef struct {
 /* Autotuner for the degree-class thresholds (the paper has no counterpart:
  * its CPU design has no degree classes).  Runs the first `sweeps` sweeps
  * of synchronous or asynchronous LPA (mode) from the identity labels on
- * graph g (device CSR, weights as in gsl_lpa) once per candidate pair of
- * warp_max in {128, 256, 512, 1024} and blk_max in {4096, 12288, 32768,
+ * graph g (device CSR, weights as in gsl_lpa) once per candidate setting:
+ * warp_max in {128, 256, 512, 1024}, blk_max in {4096, 12288, 32768,
  * 131072} with blk_max >= warp_max (pairs that bin g's vertices alike are
- * timed once), each timed with CUDA events on `stream`, and sets the
- * fastest pair on the context (the pair the context had on entry wins
- * ties).  1 <= sweeps <= 64.  Labels do not depend on the thresholds, so
+ * timed once), two-phase mode 0 or 1 (gsl_ctx_set_pregather).  Each run is
+ * timed with CUDA events on `stream`; the fastest setting is set on the
+ * context (the setting the context had on entry wins ties).  1 <= sweeps <= 64.  Labels do not depend on the thresholds, so
  * tuning changes only speed.  The context's scratch is used; the graph
  * is only read.  Synchronises `stream`.  Errors as gsl_lpa; on error the
  * entry thresholds are restored. */

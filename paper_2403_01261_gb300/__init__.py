@@ -72,7 +72,8 @@ class ServerStats(ctypes.Structure):
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("warp_max", ctypes.c_int32), ("blk_max", ctypes.c_int32), ("candidates", ctypes.c_int32),
+    _fields_ = [("warp_max", ctypes.c_int32), ("blk_max", ctypes.c_int32), ("pregather", ctypes.c_int32),
+                ("candidates", ctypes.c_int32),
                 ("sweeps", ctypes.c_int32), ("best_ms", ctypes.c_float), ("entry_ms", ctypes.c_float)]
 
 
@@ -115,6 +116,7 @@ def load():
         lib.gsl_ctx_destroy.argtypes = [P]
         lib.gsl_ctx_set_tuning.argtypes = [P, i32, i32]
         lib.gsl_autotune.argtypes = [P, cp, P, i32, i32, ctypes.POINTER(TuneResult), P]
+        lib.gsl_ctx_set_pregather.argtypes = [P, i32]
         lib.gsl_lpa.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_split.argtypes = [P, cp, P, P, i32, ctypes.POINTER(i64), P]
         lib.gsl_modularity.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
@@ -213,6 +215,10 @@ class Context:
         self._raise(self._lib.gsl_autotune(self._h, ctypes.byref(g), _ptr(weights), int(mode), int(sweeps),
                                            ctypes.byref(r), _stream(stream)))
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+    def set_pregather(self, mode: int):
+        """0: never (default), 1: when the frontier is large, 2: every eligible sweep."""
+        self._raise(self._lib.gsl_ctx_set_pregather(self._h, int(mode)))
 
     def set_batch_mode(self, use_cuda_graph: bool):
         self._raise(self._lib.gsl_ctx_set_batch_mode(self._h, int(bool(use_cuda_graph))))

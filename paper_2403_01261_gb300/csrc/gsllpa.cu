@@ -39,6 +39,8 @@ struct gsl_ctx {
 
   unsigned* rowbits = nullptr;          // row-start bitmap of the streaming identity sweep
   long long cap_rowbits = 0;
+  int* lg = nullptr;                    // labels gathered per CSR entry (two-phase sweeps)
+  long long cap_lg = 0;
   unsigned long long* wtab = nullptr;   // warp-kernel fallback tables
   long long cap_wtab = 0;
   unsigned long long* btab = nullptr;   // block-kernel fallback tables
@@ -185,12 +187,12 @@ int map_err(gsl_ctx* c, int bits, const char* where) {
 }
 
 // ------------------------------------------------------------- profiling
-enum Slot { SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + NCLASS, SL_COUNT, SL_MOD, SL_IDENT, SL_N };
+enum Slot { SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + NCLASS, SL_COUNT, SL_MOD, SL_IDENT, SL_PRE, SL_N };
 const char* slot_name(int k) {
   static const char* names[SL_N] = {"classify", "init_labels", "bin_frontier", "sweep_deg1", "sweep_deg2",
                                     "sweep_deg3_4", "sweep_deg5_8", "sweep_deg9_16", "sweep_deg17_32",
                                     "sweep_warp_small", "sweep_warp_large", "sweep_block", "sweep_hub",
-                                    "split_unionfind", "split_count_renumber", "modularity", "sweep1_stream"};
+                                    "split_unionfind", "split_count_renumber", "modularity", "sweep1_stream", "pregather"};
   return names[k];
 }
 
@@ -325,6 +327,20 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     // (rows left over by the streaming pass are not strictly increasing, so
     // the sorted-row shortcut of the hash kernels would fail on them)
     a.ident = (!async_mode && !labels_init && t == 1 && !stream1) ? 1 : 0;
+    // Two-phase sweep: gather every entry's label at full occupancy first,
+    // then the class kernels read them as a stream.  Worth it when the
+    // frontier holds most rows.
+    a.lg = nullptr;
+    if (!async_mode && !a.ident && !stream1 && g->nnz > 0 &&
+        (c->tune.pregather == 2 || (c->tune.pregather == 1 && g->nnz >= (1ll << 22) && (all_active || 4 * dn_prev > n)))) {
+      if (int r = grow(c, c->lg, c->cap_lg, g->nnz)) return r;
+      const int pe = prof_begin(c, s);
+      CK(launch_pregather(g->cols, g->nnz, a.prev, n, c->lg, c->di, s));
+      prof_end(c, pe, SL_PRE, s, 1);
+      c->profile.slot[SL_PRE].entries += g->nnz;
+      c->profile.slot[SL_PRE].bytes += 12.0 * (double)g->nnz;
+      a.lg = c->lg;
+    }
     a.check = t == 1 ? 1 : 0;
     // the first sweep that gathers labels after the identity sweep sees
     // almost as many distinct labels as neighbours (about 0.3 d on R-MAT
@@ -588,7 +604,7 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   if (!c) return GSL_OK;
   DeviceGuard dg(c->device);
   void* dptrs[] = {c->lab[0], c->lab[1], c->flag[0], c->flag[1], c->work, c->parent, c->rank, c->sigma,
-                   c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->ctr, c->sums, c->k_dev,
+                   c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->ctr, c->sums, c->k_dev,
                    c->st_off, c->st_col, c->st_w, c->st_lab};
   for (void* p : dptrs)
     if (p) cudaFree(p);
@@ -641,6 +657,7 @@ int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t m
   memset(out, 0, sizeof(*out));
   out->warp_max = entry.warp_max;
   out->blk_max = entry.blk_max;
+  out->pregather = entry.pregather;
   out->sweeps = sweeps;
   if (g->n == 0) return GSL_OK;
   DeviceGuard dg(c->device);
@@ -654,16 +671,18 @@ int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t m
   for (long long v = 0; v < g->n; ++v) deg[(size_t)v] = offs[(size_t)v + 1] - offs[(size_t)v];
   std::sort(deg.begin(), deg.end());
   std::vector<Tuning> cand{entry};
-  for (int wm : {128, 256, 512, 1024})
-    for (int bm : {4096, 12288, 32768, 131072}) {
-      if (bm < wm) continue;
-      Tuning t = entry;
-      t.warp_max = wm;
-      t.blk_max = bm;
-      bool dup = false;
-      for (const Tuning& u : cand) dup = dup || same_binning(deg, t, u);
-      if (!dup) cand.push_back(t);
-    }
+  for (int pg : {0, 1})
+    for (int wm : {128, 256, 512, 1024})
+      for (int bm : {4096, 12288, 32768, 131072}) {
+        if (bm < wm) continue;
+        Tuning t = entry;
+        t.warp_max = wm;
+        t.blk_max = bm;
+        t.pregather = pg;
+        bool dup = false;
+        for (const Tuning& u : cand) dup = dup || (u.pregather == t.pregather && same_binning(deg, t, u));
+        if (!dup) cand.push_back(t);
+      }
   auto time_one = [&](const Tuning& t, float* ms) -> int {
     c->tune = t;
     if (int r = prepare_graph(c, g, s)) return r;
@@ -698,8 +717,16 @@ int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t m
   c->tune = cand[(size_t)best];
   out->warp_max = c->tune.warp_max;
   out->blk_max = c->tune.blk_max;
+  out->pregather = c->tune.pregather;
   out->candidates = (int32_t)cand.size();
   out->best_ms = best_ms;
+  return GSL_OK;
+}
+
+int gsl_ctx_set_pregather(gsl_ctx* c, int32_t mode) {
+  if (!c) return GSL_ERR_INVALID;
+  if (mode < 0 || mode > 2) return fail(c, GSL_ERR_INVALID, "pregather mode must be 0, 1 or 2");
+  c->tune.pregather = mode;
   return GSL_OK;
 }
 

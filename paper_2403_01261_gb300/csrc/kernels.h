@@ -30,6 +30,7 @@ struct SweepArgs {
   int ident;                 // prev is the identity labelling (not read)
   int check;                 // validate weights and weighted degrees
   int mark;                  // mark neighbours of changed vertices in fnext
+  const int* lg;             // sync mode: labels gathered per entry, lg[e] = prev[col[e]] (null: gather)
 };
 
 struct Tuning {
@@ -40,6 +41,7 @@ struct Tuning {
   int group_block = 256;     // threads per block of the lane-group kernels
   int warp_block = 256;      // threads per block of the warp kernel
   int blk_block = 512;       // threads per block of the block kernel
+  int pregather = 0;         // two-phase sweeps: 0 never, 1 when the frontier is large, 2 always
 };
 
 // Degree bounds of the classes (see common.cuh).
@@ -66,6 +68,10 @@ cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool 
                                const DeviceInfo& di, cudaStream_t s);
 void count_launches(long long k);   // process-wide tally of kernels this library launched
 long long launches_total();
+// Edge-parallel label gather for a synchronous sweep: lg[e] = prev[col[e]]
+// for every CSR entry (-1 for an out-of-range column).
+cudaError_t launch_pregather(const int* col, long long nnz, const int* prev, long long n, int* lg,
+                             const DeviceInfo& di, cudaStream_t s);
 // Streaming sweep 1 (identity labels, unit weights): bits holds nnz/32+1
 // words of scratch; rows that are not strictly increasing are flagged in
 // `bad` (n bytes, zero on entry) and left for the hash kernels.

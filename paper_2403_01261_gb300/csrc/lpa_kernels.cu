@@ -129,6 +129,17 @@ __device__ __forceinline__ int gather_label(const SweepArgs& a, int j, const Pol
   return ASYNC ? ld_label_rw(a.prev + j) : ld_label_ro(a.prev + j, pol.label);
 }
 
+// Label of entry e of a row whose neighbour is j: -1 for no neighbour (past
+// the row end, out of range) and for the vertex itself (Eq. 2 skips j = i).
+// With pre-gathered labels (lp = the row's part of a.lg) the label is a
+// coalesced read of lp[e] instead of a gather.
+template <bool ASYNC>
+__device__ __forceinline__ int entry_label(const SweepArgs& a, const int* lp, int e, int j, int v, const Pol& pol) {
+  if (j < 0 || j == v) return -1;
+  if (!ASYNC && lp) return ld_stream(lp + e, pol.stream);
+  return gather_label<ASYNC>(a, j, pol);
+}
+
 template <bool ASYNC>
 __device__ __forceinline__ int own_label(const SweepArgs& a, int v) {
   if (a.ident) return v;
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a, int cls) 
     check_same_graph(a, v, j);
     const bool nb = j >= 0;
     const bool valid = nb && j != v;       // scanCommunities skips j == i
-    const int lbl = valid ? gather_label<ASYNC>(a, j, pol) : -1;
+    const int lbl = entry_label<ASYNC>(a, a.lg ? a.lg + s : nullptr, gl, j, v, pol);
     const int old = (has && gl == 0) ? own_label<ASYNC>(a, v) : 0;
     if (WEIGHTED && a.check) {
       unsigned long long ws = nb ? (unsigned long long)wt : 0ull;
@@ -389,7 +400,8 @@ __device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned c
 // group inserts.  Returns true (warp-uniform) once more than `limit`
 // distinct labels have been inserted: the table is then abandoned.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
-__device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp, int d,
+__device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
+                                         const int* lp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
                                          unsigned long long& best, unsigned long long& wsum, unsigned& own_sum) {
   const int lane = threadIdx.x & 31;
@@ -402,7 +414,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
   for (int u = 0; u < 4; ++u) {
     check_same_graph(a, v, jn[u]);
     if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-    ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+    ln[u] = entry_label<ASYNC>(a, lp, 32 * u + lane, jn[u], v, pol);
     lw[u] = wn[u];
   }
 #pragma unroll
@@ -422,7 +434,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
       for (int u = 0; u < 4; ++u) {
         check_same_graph(a, v, jn[u]);
         if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-        ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+        ln[u] = entry_label<ASYNC>(a, lp, e0 + 128 + 32 * u + lane, jn[u], v, pol);
         lw[u] = wn[u];
       }
 #pragma unroll
@@ -502,11 +514,13 @@ __global__ void __launch_bounds__(256, 3) sweep_warp_kernel(SweepArgs a, int cls
       const unsigned cap = want < (unsigned)TW ? want : (unsigned)TW;
       const unsigned limit = (!SPILL || cap >= want) ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
       unsigned own_sum = 0;
-      if (warp_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, d, tab, cap, limit, pol, best, wsum, own_sum) && SPILL) {
+      const int* lp = a.lg ? a.lg + s : nullptr;
+      if (warp_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, lp, d, tab, cap, limit, pol, best, wsum, own_sum) &&
+          SPILL) {
         best = 0;
         wsum = 0;
         own_sum = 0;
-        warp_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, own_sum);
+        warp_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, own_sum);
       }
       __syncwarp();
       if (own_sum) {   // own_sum is warp-uniform
@@ -573,7 +587,8 @@ __device__ __forceinline__ void block_publish(const SweepArgs& a, BlockRowShared
 // after the closing barrier).  The global-table pass (limit infinite) leaves
 // the flag alone, so every thread still reads the value that sent it there.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
-__device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp, int d,
+__device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
+                                         const int* lp, int d,
                                          unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
                                          BlockRowShared& sh, int par) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -589,7 +604,7 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
   for (int u = 0; u < 4; ++u) {
     check_same_graph(a, v, jn[u]);
     if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-    ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+    ln[u] = entry_label<ASYNC>(a, lp, cb + u * cu, jn[u], v, pol);
     lw[u] = wn[u];
   }
 #pragma unroll
@@ -617,7 +632,7 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
       for (int u = 0; u < 4; ++u) {
         check_same_graph(a, v, jn[u]);
         if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-        ln[u] = (jn[u] >= 0 && jn[u] != v) ? gather_label<ASYNC>(a, jn[u], pol) : -1;
+        ln[u] = entry_label<ASYNC>(a, lp, r0 + step + cb + u * cu, jn[u], v, pol);
         lw[u] = wn[u];
       }
 #pragma unroll
@@ -698,6 +713,7 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
     const int d = (int)(e - s);
     const int* cp = a.col + s;
     const int* wp = a.w + s;
+    const int* lp = a.lg ? a.lg + s : nullptr;
     int sorted = 0;
     if (a.ident && !ASYNC) {
       unsigned long long best = 0, wsum = 0;
@@ -719,9 +735,9 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
         const unsigned cap = want < tb ? want : tb;
         // each of up to 16 warps may add 32 new slots after the flag is raised
         const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, d, smem_b64, cap, limit, pol, sh, par);
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, lp, d, smem_b64, cap, limit, pol, sh, par);
       }
-      if (ovf) block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
+      if (ovf) block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
     }
     unsigned long long b = sh.best[par];
     const unsigned own_sum = sh.own[par];
@@ -752,6 +768,43 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
     v1 = v2;
   }
   flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// ---------------------------------------------------------------------------
+// Edge-parallel gather of a synchronous sweep's neighbour labels.  The class
+// kernels hold hash tables in shared memory, which caps their occupancy,
+// and they interleave dependent loads with hashing; this pass has neither:
+// every thread keeps four independent gathers in flight at full occupancy,
+// and the class kernels then read the labels as a coalesced stream.
+__global__ void __launch_bounds__(256) pregather_kernel(const int* __restrict__ col, long long nnz,
+                                                        const int* __restrict__ prev, long long n,
+                                                        int* __restrict__ lg) {
+  const unsigned long long ps = policy_evict_first(), pl = policy_evict_last();
+  const long long st = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * st < nnz; i += 4 * st) {
+    int j[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) j[u] = ld_stream(col + i + u * st, ps);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) l[u] = (unsigned)j[u] < (unsigned)n ? ld_label_ro(prev + j[u], pl) : -1;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) __stcs(lg + i + u * st, l[u]);
+  }
+  for (; i < nnz; i += st) {
+    const int j = ld_stream(col + i, ps);
+    __stcs(lg + i, (unsigned)j < (unsigned)n ? ld_label_ro(prev + j, pl) : -1);
+  }
+}
+
+cudaError_t launch_pregather(const int* col, long long nnz, const int* prev, long long n, int* lg,
+                             const DeviceInfo& di, cudaStream_t s) {
+  if (nnz <= 0) return cudaSuccess;
+  long long blocks = (nnz + 255) / 256;
+  const long long cap = 16ll * di.sm_count;
+  pregather_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(col, nnz, prev, n, lg);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

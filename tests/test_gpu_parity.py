@@ -45,6 +45,22 @@ def small_ctx(gpu_lib):
     return c
 
 
+@pytest.fixture(scope="module")
+def variants(ctx, small_ctx, gpu_lib):
+    """Default thresholds, tiny thresholds, and both with two-phase sweeps
+    forced on (labels gathered per entry before the class kernels run)."""
+    pre = gpu_lib.Context(0)
+    pre.set_pregather(2)
+    small_pre = gpu_lib.Context(0)
+    small_pre.set_tuning(32, 48)
+    small_pre.set_pregather(2)
+    never = gpu_lib.Context(0)
+    never.set_pregather(0)
+    return {"default": ctx, "small": small_ctx, "pre": pre, "small_pre": small_pre, "never": never}
+
+
+VARIANTS = ["default", "small", "pre", "small_pre", "never"]
+
 GRAPHS = {
     "two_k5": lambda: I.two_cliques_bridge(5),
     "path9": lambda: I.path(9),
@@ -64,11 +80,11 @@ def graph(request):
 
 
 # ----------------------------------------------------------------- sync LPA
-@pytest.mark.parametrize("use_small", [False, True])
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("w", [False, True])
-def test_sync_lpa_bit_exact(graph, ctx, small_ctx, use_small, w):
+def test_sync_lpa_bit_exact(graph, variants, variant, w):
     g = weighted(graph) if w else graph
-    c = small_ctx if use_small else ctx
+    c = variants[variant]
     off, col, wt = dev(g)
     got, st = c.lpa(off, col, wt, tolerance=0.05, max_iters=20, stats=True)
     want, t, dn = O.lpa_sync(g, 0.05, 20)
@@ -77,12 +93,12 @@ def test_sync_lpa_bit_exact(graph, ctx, small_ctx, use_small, w):
     assert np.array_equal(got.cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("use_small", [False, True])
-def test_one_sweep_from_random_labels(graph, ctx, small_ctx, use_small):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_one_sweep_from_random_labels(graph, variants, variant):
     rng = np.random.default_rng(7)
     for w in (False, True):
         g = weighted(graph, 3) if w else graph
-        c = small_ctx if use_small else ctx
+        c = variants[variant]
         off, col, wt = dev(g)
         for k in (2, max(2, g.n // 50), g.n):
             prev = rng.integers(0, min(k, g.n), g.n).astype(np.int32)
@@ -237,7 +253,7 @@ def test_max_iters_zero_and_self_loops(ctx):
     assert abs(ctx.modularity(off, col, lab) - O.modularity(g, lab.cpu().numpy())) < 1e-12
 
 
-def test_duplicate_entries_unsorted_rows(ctx, small_ctx):
+def test_duplicate_entries_unsorted_rows(variants):
     rng = np.random.default_rng(5)
     g = I.rmat(12, 16, seed=3)
     # shuffle each row and duplicate some entries (both directions, so still symmetric)
@@ -254,7 +270,7 @@ def test_duplicate_entries_unsorted_rows(ctx, small_ctx):
     offsets = np.cumsum(offsets)
     h = I.Graph(offsets, allp[:, 1].astype(np.int32), name="rmat12-dup-unsorted")
     off, col, _ = dev(h)
-    for c in (ctx, small_ctx):
+    for c in variants.values():
         got, st = c.lpa(off, col, stats=True)
         want, t, dn = O.lpa_sync(h, 0.05, 20)
         assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
@@ -282,12 +298,12 @@ def _mixed_rows(seed=7):
     return I.Graph(offsets, cols, name="rmat13-mixed-rows")
 
 
-def test_first_sweep_mixed_rows(ctx, small_ctx):
+def test_first_sweep_mixed_rows(variants):
     h = _mixed_rows()
     d = np.diff(h.offsets)
     assert d.max() > 512 and (d == 0).any()
     off, col, _ = dev(h)
-    for c in (ctx, small_ctx):
+    for c in variants.values():
         for iters in (1, 2):
             want, t, dn = O.lpa_sync(h, 0.0, iters)
             got, st = c.lpa(off, col, tolerance=0.0, max_iters=iters, stats=True)
@@ -298,7 +314,7 @@ def test_first_sweep_mixed_rows(ctx, small_ctx):
         assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
 
 
-def test_invalid_inputs_are_rejected(ctx, gpu_lib):
+def test_invalid_inputs_are_rejected(ctx, gpu_lib, variants):
     g = I.path(6)
     off, col, _ = dev(g)
     bad_col = col.clone()
@@ -306,6 +322,13 @@ def test_invalid_inputs_are_rejected(ctx, gpu_lib):
     with pytest.raises(gpu_lib.GslError) as e:
         ctx.lpa(off, bad_col)
     assert e.value.code == 1
+    start = torch.arange(6, dtype=torch.int32, device=DEV).flip(0).contiguous()
+    for name in ("pre", "small_pre"):   # the two-phase path reports it too
+        with pytest.raises(gpu_lib.GslError) as e:
+            variants[name].lpa(off, bad_col, labels_init=start)
+        assert e.value.code == 1
+    with pytest.raises(gpu_lib.GslError):
+        variants["pre"].set_pregather(3)
     bad_off = off.clone()
     bad_off[2] = 1
     bad_off[3] = 0
