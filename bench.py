@@ -50,11 +50,40 @@ def parse():
     p.add_argument("--cache", default=os.environ.get("GSL_BENCH_CACHE", os.path.join(tempfile.gettempdir(),
                                                                                     "gsl_bench_cache")))
     p.add_argument("--profile-json", default="", help="also write the per-slot profile here")
-    p.add_argument("--workload", choices=["rmat", "batched"], default="rmat",
+    p.add_argument("--workload", choices=["rmat", "batched", "served"], default="rmat",
                    help="rmat: one R-MAT graph (default); batched: many SBM graphs per call vs one call per graph")
     p.add_argument("--graphs", type=int, default=4096, help="graphs in the batched workload")
     p.add_argument("--gen-procs", type=int, default=0, help="host processes generating the batched graphs")
+    p.add_argument("--rate", type=float, default=2000.0, help="served: mean Poisson arrival rate (requests/s)")
+    p.add_argument("--duration", type=float, default=5.0, help="served: seconds of arrivals per rate")
+    p.add_argument("--pool", type=int, default=48, help="served: distinct request graphs (drawn with replacement)")
+    p.add_argument("--slots", type=int, default=3, help="served: concurrent batches of the server")
     return p.parse_args()
+
+
+# ------------------------------------------------------------------- ranks
+def rank_env():
+    """(rank, world, local_rank) from the launcher's environment (torchrun
+    sets RANK / WORLD_SIZE / LOCAL_RANK; a plain run is rank 0 of 1)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest of every rank's x (each rank passes its own step time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(world, units_per_rank, ms):
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank units, timed by the slowest rank (ms)."""
+    return world * units_per_rank / (ms * 1e-3)
 
 
 # ------------------------------------------------------------------ workload
@@ -167,7 +196,7 @@ def cpu_baseline(scale, edge_factor, tol, max_iters):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    rank = rank_env()[0]
     if rank != 0:
         return 0
     import oracle  # noqa: F401  (builds the oracle)
@@ -286,6 +315,130 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
     return 0
 
+# -------------------------------------------------------------- served mode
+def _gen_served(ks):
+    import inputs as I
+    out = []
+    for k in ks:
+        g = I.served_request(k, threads=1)
+        out.append((k, g.offsets, g.cols))
+    return out
+
+
+def served_pool(count, procs):
+    """Request graphs 0..count-1 of the served workload (inputs.served_request)."""
+    import multiprocessing as mp
+    procs = procs or max(1, min(16, os.cpu_count() or 1))
+    chunks = [list(range(p, count, procs)) for p in range(procs)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        parts = pool.map(_gen_served, chunks)
+    got = sorted((x for part in parts for x in part), key=lambda x: x[0])
+    return [(o, c) for _, o, c in got]
+
+
+def _serve_at(srv, pool, rate, duration, seed):
+    """Poisson arrivals at `rate` for `duration` s, each a random pool graph;
+    returns per-request (pool index, request info, labels of the first few)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=int(rate * duration * 1.5) + 16)
+    times = np.cumsum(gaps)
+    times = times[times < duration]
+    picks = rng.integers(0, len(pool), size=len(times))
+    ids = [None] * len(times)
+    submitted = threading.Event()
+    t_start = time.perf_counter()
+
+    def submitter():
+        for i, (t, k) in enumerate(zip(times, picks)):
+            delay = t_start + t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = srv.submit(*pool[k])
+        submitted.set()
+
+    th = threading.Thread(target=submitter, daemon=True)
+    th.start()
+    infos, labels = [], {}
+    for i in range(len(times)):
+        while ids[i] is None:
+            time.sleep(0.0002)
+        lab, info = srv.wait(ids[i], info=True)
+        infos.append(info)
+        if int(picks[i]) not in labels:
+            labels[int(picks[i])] = lab.copy()
+    t_end = time.perf_counter()
+    th.join()
+    return picks, infos, labels, t_end - t_start
+
+
+def run_served(args):
+    """Served workload: Poisson arrivals of request graphs (70 % planted
+    partition, 30 % R-MAT, n log-uniform 1e3..2^22) from a pinned host pool,
+    through the library's continuous-batching server; against one
+    gsl_gsllpa_host call per request, one at a time."""
+    import numpy as np
+    import torch
+    t0 = time.time()
+    raw = served_pool(args.pool, args.gen_procs)
+    gen_s = time.time() - t0
+    torch.cuda.set_device(0)
+    import paper_2403_01261_gb300 as gsl
+    pool, keep = [], []
+    for o, c in raw:
+        to, tc = torch.from_numpy(o).pin_memory(), torch.from_numpy(c).pin_memory()
+        keep.append((to, tc))
+        pool.append((to.numpy(), tc.numpy()))
+    # plain: one request at a time through the host-buffer entry point
+    ctx = gsl.Context(0)
+    outs = [torch.empty(o.shape[0] - 1, dtype=torch.int32).pin_memory() for o, _ in pool]
+    for (o, c), lab in list(zip(keep, outs))[:4]:
+        ctx.gsllpa_host(o, c, out=lab)
+    p0 = time.perf_counter()
+    for (o, c), lab in zip(keep, outs):
+        ctx.gsllpa_host(o, c, out=lab)
+    plain_s = time.perf_counter() - p0
+    plain_gps = len(pool) / plain_s
+    ctx.close()
+    srv = gsl.Server(device=0, slots=args.slots, memory_fraction=0.6, tolerance=0.05, max_iters=20)
+    for k in range(min(4, len(pool))):     # warm-up
+        srv.wait(srv.submit(*pool[k]))
+    runs = []
+    launches0 = gsl.kernel_launches()
+    with ClockSampler(0) as clk:
+        for rate in (args.rate, None):
+            if rate is None:   # a second, lighter load where p99 is not queueing-dominated
+                rate = 0.5 * min(args.rate, runs[0]["achieved_rps"])
+            picks, infos, labels, wall = _serve_at(srv, pool, rate, args.duration, seed=len(runs))
+            lat = np.array([i["latency_ms"] for i in infos])
+            runs.append({"offered_rps": rate, "requests": len(infos), "achieved_rps": len(infos) / wall,
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "mean_batch_graphs": float(np.mean([i["batch_graphs"] for i in infos])),
+                         "same_as_plain": all(np.array_equal(lab, outs[k].numpy()) for k, lab in labels.items())})
+    launches = gsl.kernel_launches() - launches0
+    st = srv.stats()
+    srv.close()
+    nnz = np.array([c.shape[0] for _, c in pool])
+    line = {
+        "metric": "served GSL-LPA graphs/s with p50/p99 latency (Poisson arrivals, continuous batching)",
+        "value": runs[0]["achieved_rps"], "unit": "graphs/s", "n_gpus": 1, "steps": len(runs), "warmup": 4,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"served-pool{len(pool)}", "rate_rps": args.rate, "duration_s": args.duration,
+                   "slots": args.slots, "mix": "70% planted partition / 30% R-MAT ef16, n log-uniform 1e3..2^22",
+                   "mean_nnz": float(nnz.mean()), "tolerance": 0.05, "max_iters": 20, "mode": "sync"},
+        "p50_ms": runs[0]["p50_ms"], "p99_ms": runs[0]["p99_ms"], "runs": runs,
+        "plain": {"value": plain_gps, "unit": "graphs/s", "how": "one gsl_gsllpa_host call per pool graph, pinned"},
+        "speedup_vs_plain": runs[0]["achieved_rps"] / plain_gps,
+        "labels_identical_to_plain": all(r["same_as_plain"] for r in runs),
+        "server": st, "gpu_launches": launches, "generation_s": gen_s, "clocks": clk.summary(),
+        "e2e": {"value": runs[0]["achieved_rps"], "unit": "graphs/s",
+                "h2d_bytes_per_step": int(8 * sum(o.shape[0] for o, _ in pool) + 4 * nnz.sum()) // len(pool),
+                "d2h_bytes_per_step": int(4 * sum(o.shape[0] - 1 for o, _ in pool)) // len(pool)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU side
 def dominant_roofline(profile, peaks):
     slots = [s for s in profile if s["ms"] > 0 and s["bytes"] > 0]
@@ -326,11 +479,11 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     import numpy as np
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -379,10 +532,7 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     prof = ctx.profile()
     ctx.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
 
     # end to end through the host-buffer entry point (copies inside the region)
     e2e = None
@@ -401,11 +551,8 @@ def main():
         torch.cuda.synchronize(dev)
         wall = (time.perf_counter() - t0) / args.e2e_steps
         e2e_ms = max(e0.elapsed_time(e1) / args.e2e_steps, wall * 1e3)
-        if world > 1:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * nnz / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
+        e2e_ms = max_over_ranks(e2e_ms, world, dev)
+        e2e = {"value": replicas_value(world, nnz, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
                "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms}
         if mode == 0:
             assert torch.equal(lab_h, out.cpu()), "host-buffer path disagrees with the device path"
@@ -427,7 +574,7 @@ def main():
         cpu.pop("seconds", None)
     clocks = clk.summary()
     line = {
-        "metric": METRIC, "value": world * nnz / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": replicas_value(world, nnz, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"rmat{args.scale}-ef{args.edge_factor}", "rmat_abcd": [0.57, 0.19, 0.19, 0.05],

@@ -173,6 +173,39 @@ int gsl_lpa(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, const int32_
 int gsl_split(gsl_ctx* ctx, const gsl_csr* g, const int32_t* labels_in, int32_t* labels_out,
               int32_t renumber, int64_t* k_out, void* stream);
 
+/* Split by label propagation: splitDisconnectedLp() of Algorithm 1 (SL-LP,
+ * or SL-LPP with pruning).  labels_out starts as the vertex ids; every sweep
+ * each vertex (with pruning: each vertex of the frontier, initially all)
+ * takes the smallest labels_out value over itself and its neighbours with
+ * the same labels_in value, in place; with pruning a vertex that changed
+ * puts those neighbours in the next frontier.  Sweeps repeat until one
+ * changes nothing.  The fixed point is the labelling gsl_split returns with
+ * renumber = 0 (the smallest vertex id of every piece); the number of sweeps
+ * depends on the update order and is not deterministic.
+ *   labels_in   device int32[n], any values (only compared for equality).
+ *   labels_out  device int32[n]; must not overlap labels_in.
+ *   pruning     0: SL-LP, 1: SL-LPP.
+ *   sweeps_out  optional HOST pointer receiving the sweeps run (the last one
+ *               changes nothing).
+ * Synchronises `stream` after every sweep (the stop test reads the change
+ * count).  Errors: GSL_ERR_INVALID for bad arguments or columns;
+ * GSL_ERR_TIMEOUT if more than n + 1 sweeps would be needed (cannot happen
+ * on valid input). */
+int gsl_split_lp(gsl_ctx* ctx, const gsl_csr* g, const int32_t* labels_in, int32_t* labels_out, int32_t pruning,
+                 int32_t* sweeps_out, void* stream);
+
+/* Disconnected communities: disconnectedCommunities() of Algorithm 4.  A
+ * community (a labels value) is disconnected when the subgraph of edges
+ * inside it has more than one connected piece.
+ *   labels      device int32[n], values in [0, n) (else GSL_ERR_INVALID).
+ *   flags_out   optional device uint8[n]: flags_out[c] = 1 for every
+ *               disconnected community c, else 0.
+ *   count_out   HOST pointer receiving the number of disconnected
+ *               communities.
+ * Uses the union-find of gsl_split; synchronises `stream`. */
+int gsl_disconnected(gsl_ctx* ctx, const gsl_csr* g, const int32_t* labels, uint8_t* flags_out, int64_t* count_out,
+                     void* stream);
+
 /* Modularity, Eq. 1:  Q = sum_c [ sigma_c / 2m - (Sigma_c / 2m)^2 ], with
  * 2m the sum of all entry weights, sigma_c the weight of entries inside c
  * and Sigma_c the summed weighted degree of c's vertices.  The three sums

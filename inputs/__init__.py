@@ -229,6 +229,37 @@ def batched_sbm(g: int, threads=None, **kw):
     return sbm(n, bs, prm["p_in"], prm["p_out"], seed=g, threads=threads, name=f"batched-sbm-{g}")
 
 
+def served_request_params(k: int, n_lo=1_000, n_hi=4_194_304, sbm_share=0.7):
+    """Request k of the served workload (seed k): with probability sbm_share
+    a planted partition with the batched laws for blocks, degree and ratio,
+    else an R-MAT of scale clamp(round(log2 n), 10, 22) and edge factor 16;
+    n log-uniform in [n_lo, n_hi]."""
+    lib = _lib()
+    s = 0x53525644  # stream id of the served-request draws
+    lo, hi = lib.gg_det_log(float(n_lo)), lib.gg_det_log(float(n_hi))
+    n = int(lib.gg_det_exp(lo + (hi - lo) * lib.gg_u01(k, s, 1)) + 0.5)
+    if lib.gg_u01(k, s, 0) >= sbm_share:
+        scale = min(22, max(10, int(round(float(np.log2(n))))))
+        return dict(kind="rmat", scale=scale, edge_factor=16, n=1 << scale)
+    nb = min(n, 5 + int(lib.gg_below(k, s, 2, 196)))
+    d = 8.0 + 32.0 * lib.gg_u01(k, s, 3)
+    r = 3.0 + 9.0 * lib.gg_u01(k, s, 4)
+    size = n / nb
+    d_in, d_out = d * r / (r + 1.0), d / (r + 1.0)
+    p_in = d_in / (size - 1.0) if size > 1.0 else 0.0
+    p_out = d_out / (n - size) if n > size else 0.0
+    return dict(kind="sbm", n=n, blocks=nb, degree=d, ratio=r, p_in=min(p_in, 1.0), p_out=min(p_out, 1.0))
+
+
+def served_request(k: int, threads=None, **kw):
+    prm = served_request_params(k, **kw)
+    if prm["kind"] == "rmat":
+        return rmat(prm["scale"], prm["edge_factor"], seed=1000 + k, threads=threads)
+    n, nb = prm["n"], prm["blocks"]
+    bs = (np.arange(nb + 1, dtype=np.int64) * n) // nb
+    return sbm(n, bs, prm["p_in"], prm["p_out"], seed=1000 + k, threads=threads, name=f"served-sbm-{k}")
+
+
 # ---------------------------------------------------------------- hand-built graphs
 def from_edges(n, edges, weights=None, name=""):
     """Symmetric CSR from an undirected edge list; both directions carry the

@@ -117,6 +117,8 @@ def load():
         lib.gsl_ctx_set_tuning.argtypes = [P, i32, i32]
         lib.gsl_autotune.argtypes = [P, cp, P, i32, i32, ctypes.POINTER(TuneResult), P]
         lib.gsl_ctx_set_pregather.argtypes = [P, i32]
+        lib.gsl_split_lp.argtypes = [P, cp, P, P, i32, ctypes.POINTER(i32), P]
+        lib.gsl_disconnected.argtypes = [P, cp, P, P, ctypes.POINTER(i64), P]
         lib.gsl_lpa.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_split.argtypes = [P, cp, P, P, i32, ctypes.POINTER(i64), P]
         lib.gsl_modularity.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
@@ -260,6 +262,30 @@ class Context:
                                  ctypes.byref(k), _stream(stream))
         self._raise(rc)
         return out, int(k.value)
+
+    def split_lp(self, offsets, cols, labels, pruning=False, out=None, stream=None):
+        """Algorithm 1 (SL-LP, or SL-LPP with pruning) -> (labels, sweeps)."""
+        import torch
+        g = _check_graph(offsets, cols)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        t = ctypes.c_int32()
+        rc = self._lib.gsl_split_lp(self._h, ctypes.byref(g), _ptr(labels), _ptr(out), int(bool(pruning)),
+                                    ctypes.byref(t), _stream(stream))
+        self._raise(rc)
+        return out, int(t.value)
+
+    def disconnected(self, offsets, cols, labels, flags=False, stream=None):
+        """Algorithm 4 -> number of disconnected communities (and, with
+        flags=True, a uint8 tensor flagging them)."""
+        import torch
+        g = _check_graph(offsets, cols)
+        f = torch.zeros(g.n, dtype=torch.uint8, device=offsets.device) if flags else None
+        k = ctypes.c_int64()
+        rc = self._lib.gsl_disconnected(self._h, ctypes.byref(g), _ptr(labels), _ptr(f), ctypes.byref(k),
+                                        _stream(stream))
+        self._raise(rc)
+        return (int(k.value), f) if flags else int(k.value)
 
     def modularity(self, offsets, cols, labels, weights=None, stream=None):
         g = _check_graph(offsets, cols, weights)

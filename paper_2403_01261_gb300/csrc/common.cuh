@@ -76,6 +76,14 @@ __device__ __forceinline__ int ld_stream(const int* p, unsigned long long pol) {
   return v;
 }
 __device__ __forceinline__ int ld_stream(const int* p) { return ld_stream(p, policy_evict_first()); }
+// 16-byte streaming load (p must be 16-byte aligned).
+__device__ __forceinline__ int4 ld_stream4(const int4* p, unsigned long long pol) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
 // Gather of a label that stays constant for the whole kernel (Jacobi sweep):
 // read-only path, L2 evict-last policy.
 __device__ __forceinline__ int ld_label_ro(const int* p, unsigned long long pol) {
@@ -89,6 +97,22 @@ __device__ __forceinline__ int ld_label_ro(const int* p) { return ld_label_ro(p,
 __device__ __forceinline__ int ld_label_rw(const int* p) { return __ldcg(p); }
 
 __device__ __forceinline__ uint32_t hash32(uint32_t x) { return x * 0x9E3779B1u; }
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(FULL, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+
 
 __host__ __device__ __forceinline__ unsigned next_pow2(unsigned x) {
   unsigned p = 1;

@@ -800,6 +800,67 @@ int gsl_split(gsl_ctx* c, const gsl_csr* g, const int32_t* labels_in, int32_t* l
   return GSL_OK;
 }
 
+int gsl_split_lp(gsl_ctx* c, const gsl_csr* g, const int32_t* labels_in, int32_t* labels_out, int32_t pruning,
+                 int32_t* sweeps_out, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_csr(c, g)) return r;
+  if (g->n > 0 && (!labels_in || !labels_out)) return fail(c, GSL_ERR_INVALID, "labels pointer is NULL");
+  if (g->n > 0 && labels_in == labels_out) return fail(c, GSL_ERR_INVALID, "labels_out must not overlap labels_in");
+  if (pruning != 0 && pruning != 1) return fail(c, GSL_ERR_INVALID, "pruning must be 0 or 1");
+  if (sweeps_out) *sweeps_out = 0;
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = g->n;
+  if (int r = ensure_vertex_scratch(c, n)) return r;
+  if (int r = prepare_graph(c, g, s)) return r;   // validates the offsets
+  CK(launch_split_lp_init(labels_out, pruning ? c->flag[0] : nullptr, n, c->di, s));
+  if (pruning) CK(cudaMemsetAsync(c->flag[1], 0, (size_t)n, s));
+  int t = 0;
+  for (;;) {
+    if (t > n) return fail(c, GSL_ERR_TIMEOUT, "split_lp: no fixed point after n + 1 sweeps");
+    ++t;
+    if (int r = reset_sweep_counters(c, s)) return r;
+    const int pe = prof_begin(c, s);
+    CK(launch_split_lp_sweep(OFF(g), g->cols, labels_in, n, labels_out, c->flag[(t - 1) & 1], c->flag[t & 1],
+                             pruning, c->ctr, c->di, s));
+    prof_end(c, pe, SL_SPLIT, s, 1);
+    CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    prof_resolve(c);
+    if (int r = map_err(c, c->ctr_h->err, "split_lp")) return r;
+    if (c->ctr_h->dn == 0) break;
+  }
+  if (sweeps_out) *sweeps_out = t;
+  return GSL_OK;
+}
+
+int gsl_disconnected(gsl_ctx* c, const gsl_csr* g, const int32_t* labels, uint8_t* flags_out, int64_t* count_out,
+                     void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_csr(c, g)) return r;
+  if (!count_out) return fail(c, GSL_ERR_INVALID, "count_out is NULL");
+  if (g->n > 0 && !labels) return fail(c, GSL_ERR_INVALID, "labels is NULL");
+  *count_out = 0;
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = g->n;
+  if (int r = ensure_vertex_scratch(c, n)) return r;
+  if (int r = prepare_graph(c, g, s)) return r;
+  long long k = 0;
+  if (int r = run_split(c, g, labels, c->lab[0], 0, &k, s)) return r;
+  CK(launch_disconnected(c->lab[0], labels, n, c->lab[1], flags_out, c->k_dev, c->ctr, c->di, s));
+  CK(cudaMemcpyAsync(c->k_h, c->k_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (int r = map_err(c, c->ctr_h->err, "disconnected")) return r;
+  *count_out = (int64_t)*c->k_h;
+  return GSL_OK;
+}
+
 int gsl_modularity(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t* labels, double* q_out,
                    void* stream) {
   if (!c) return GSL_ERR_INVALID;

@@ -102,6 +102,17 @@ cudaError_t launch_renumber(const int* rep, int* out, long long n, int* rank, un
                             long long nblocks_cap, unsigned long long* k_dev, const DeviceInfo& di,
                             cudaStream_t s);
 long long renumber_blocks(long long n);
+// Algorithm 4 from split representatives: cnt (n ints) receives the pieces
+// per community, flags (nullable, n bytes) the disconnected communities,
+// *total their number.
+cudaError_t launch_disconnected(const int* rep, const int* labels, long long n, int* cnt, unsigned char* flags,
+                                unsigned long long* total, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+// Algorithm 1: cp = identity (and every frontier flag set), then sweeps
+// until Counters::dn stays zero.
+cudaError_t launch_split_lp_init(int* cp, unsigned char* f, long long n, const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_split_lp_sweep(const long long* off, const int* col, const int* labels, long long n, int* cp,
+                                  unsigned char* fcur, unsigned char* fnext, int prune, Counters* ctr,
+                                  const DeviceInfo& di, cudaStream_t s);
 
 // modularity_kernels.cu
 struct ModSums {

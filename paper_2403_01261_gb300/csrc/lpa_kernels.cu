@@ -49,21 +49,6 @@ __device__ __forceinline__ unsigned long long pack_key(unsigned sum, int lbl) {
   return ((unsigned long long)sum << 32) | (unsigned long long)(~(unsigned)lbl);
 }
 
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    unsigned long long y = __shfl_xor_sync(FULL, x, o);
-    x = y > x ? y : x;
-  }
-  return x;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-  return x;
-}
-
 // Adds the per-thread sweep statistics of the whole block to the counters.
 __device__ __forceinline__ void flush_counters(Counters* ctr, int cls, unsigned long long dn,
                                                unsigned long long scanned) {
@@ -836,33 +821,60 @@ __device__ __forceinline__ long long row_of(const long long* off, long long n, l
   return lo;
 }
 
+// Entry e (column je) against entry e + 1 (column jn): the row is not
+// strictly increasing if e + 1 continues e's row and jn <= je.
+__device__ __forceinline__ void check_pair(const long long* off, long long n, long long nnz, const unsigned* bits,
+                                           unsigned char* bad, Counters* ctr, long long e, int je, int jn) {
+  if ((unsigned)je >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
+  const long long f = e + 1;
+  if (f < nnz && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0 && !(je < jn)) bad[row_of(off, n, e)] = 1;
+}
+
+// Sixteen entries per thread per round, as four 16-byte loads issued
+// together; the few entries before the first 16-byte boundary and after the
+// last whole quad are checked by one thread.  The entry after a thread's
+// quad comes from the next lane (or the next quad row of the warp).
 __global__ void __launch_bounds__(256) sorted_check_kernel(const long long* __restrict__ off, long long n,
                                                             const int* __restrict__ col, long long nnz,
                                                             const unsigned* __restrict__ bits,
                                                             unsigned char* __restrict__ bad, Counters* ctr) {
   const unsigned long long pol = policy_evict_first();
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  long long head = (long long)((16 - ((unsigned long long)col & 15)) & 15) >> 2;   // col is 4-byte aligned
+  if (head > nnz) head = nnz;
+  const long long nq = (nnz - head) >> 2;
+  const long long tail0 = head + 4 * nq;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid == 0) {
+    for (long long e = 0; e < head; ++e) check_pair(off, n, nnz, bits, bad, ctr, e, col[e], e + 1 < nnz ? col[e + 1] : 0);
+    for (long long e = tail0; e < nnz; ++e)
+      check_pair(off, n, nnz, bits, bad, ctr, e, col[e], e + 1 < nnz ? col[e + 1] : 0);
+  }
+  const int4* cq = reinterpret_cast<const int4*>(col + head);
+  const long long warp = tid >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long e0 = warp * 128; e0 < nnz; e0 += nwarps * 128) {
-    int j[4];
+  for (long long qb = warp * 128; qb < nq; qb += nwarps * 128) {   // warp-uniform; 128 quads per round
+    int4 v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const long long e = e0 + 32 * u + lane;
-      j[u] = e < nnz ? ld_stream(col + e, pol) : 0;
+      const long long q = qb + u * 32 + lane;
+      v[u] = q < nq ? ld_stream4(cq + q, pol) : make_int4(0, 0, 0, 0);
     }
-    const int tail = (lane == 31 && e0 + 128 < nnz) ? ld_stream(col + e0 + 128, pol) : 0;
+    const long long elast = head + 4 * (qb + 128);   // the entry after the round's last quad
+    const int tailx = (lane == 31 && qb + 128 <= nq && elast < nnz) ? ld_stream(col + elast, pol) : 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const long long e = e0 + 32 * u + lane;
-      int nxt = __shfl_down_sync(FULL, j[u], 1);
-      const int head = u < 3 ? __shfl_sync(FULL, j[u < 3 ? u + 1 : u], 0) : tail;
-      if (lane == 31) nxt = head;
-      if (e < nnz) {
-        if ((unsigned)j[u] >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
-        const long long f = e + 1;
-        const bool row_continues = f < nnz && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0;
-        if (row_continues && !(j[u] < nxt)) bad[row_of(off, n, e)] = 1;
+      int nx = __shfl_down_sync(FULL, v[u].x, 1);
+      const int hx = u < 3 ? __shfl_sync(FULL, v[u < 3 ? u + 1 : u].x, 0) : tailx;
+      if (lane == 31) nx = hx;
+      const long long q = qb + u * 32 + lane;
+      if (q < nq) {
+        const long long e = head + 4 * q;
+        if (q + 1 >= nq) nx = e + 4 < nnz ? col[e + 4] : 0;   // the next entry lies in the scalar tail
+        check_pair(off, n, nnz, bits, bad, ctr, e, v[u].x, v[u].y);
+        check_pair(off, n, nnz, bits, bad, ctr, e + 1, v[u].y, v[u].z);
+        check_pair(off, n, nnz, bits, bad, ctr, e + 2, v[u].z, v[u].w);
+        check_pair(off, n, nnz, bits, bad, ctr, e + 3, v[u].w, nx);
       }
     }
   }

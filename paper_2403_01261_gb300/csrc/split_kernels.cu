@@ -255,6 +255,95 @@ __global__ void rn_apply_kernel(const int* __restrict__ rep, int* __restrict__ o
     out[v] = rank[rep[v]];
 }
 
+// ------------------------------------------------------------ Algorithm 4
+// A community is disconnected when it holds more than one piece.  With the
+// pieces from the union-find (every piece labelled by its smallest vertex),
+// each piece representative adds one to its community's count; flags are
+// the communities with a count of two or more.
+__global__ void disc_count_kernel(const int* __restrict__ rep, const int* __restrict__ labels, long long n,
+                                  int* __restrict__ cnt, Counters* ctr) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int c = labels[v];
+    if ((unsigned)c >= (unsigned)n) {
+      raise_err(&ctr->err, ERRBIT_INVALID);
+      continue;
+    }
+    if (rep[v] == (int)v) atomicAdd(cnt + c, 1);
+  }
+}
+
+__global__ void disc_flag_kernel(const int* __restrict__ cnt, long long n, unsigned char* __restrict__ flags,
+                                 unsigned long long* total) {
+  unsigned long long mine = 0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const bool f = cnt[c] >= 2;
+    if (flags) flags[c] = f ? 1 : 0;
+    mine += f ? 1ull : 0ull;
+  }
+  mine = warp_sum_u64(mine);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(total, mine);
+}
+
+// ------------------------------------------------------------ Algorithm 1
+// One sweep of SL-LP / SL-LPP: every vertex (with pruning: every vertex of
+// the current frontier) takes the smallest piece label over itself and its
+// neighbours of the same community, in place.  A warp handles a vertex;
+// labels only decrease, so concurrent updates converge to the same fixed
+// point as the sequential sweep: the smallest vertex id of every piece.
+// With pruning, a vertex that changed puts its same-community neighbours in
+// the next frontier.
+__global__ void __launch_bounds__(256) split_lp_kernel(const long long* __restrict__ off, const int* __restrict__ col,
+                                                       const int* __restrict__ labels, long long n, int* cp,
+                                                       unsigned char* __restrict__ fcur,
+                                                       unsigned char* __restrict__ fnext, int prune, Counters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_dn = 0;
+  for (long long v = warp; v < n; v += nwarps) {
+    if (prune) {
+      if (!fcur[v]) continue;   // warp-uniform
+      __syncwarp();
+      if (lane == 0) fcur[v] = 0;
+    }
+    const long long s = off[v], e = off[v + 1];
+    const int c = labels[v];
+    const int cur = __ldcg(cp + v);
+    int m = cur;
+    for (long long x = s + lane; x < e; x += 32) {
+      const int j = ld_stream(col + x);
+      if ((unsigned)j >= (unsigned)n) {
+        raise_err(&ctr->err, ERRBIT_INVALID);
+        continue;
+      }
+      if (ld_label_ro(labels + j) == c) {
+        const int pj = __ldcg(cp + j);
+        m = pj < m ? pj : m;
+      }
+    }
+    m = __reduce_min_sync(FULL, m);
+    if (m < cur) {   // warp-uniform
+      if (lane == 0) __stcg(cp + v, m);
+      my_dn += lane == 0 ? 1ull : 0ull;
+      if (prune) {
+        for (long long x = s + lane; x < e; x += 32) {
+          const int j = ld_stream(col + x);
+          if ((unsigned)j < (unsigned)n && ld_label_ro(labels + j) == c) fnext[j] = 1;
+        }
+      }
+    }
+  }
+  my_dn = warp_sum_u64(my_dn);
+  if (lane == 0 && my_dn) atomicAdd(&ctr->dn, my_dn);
+}
+
+__global__ void iota_kernel(int* __restrict__ p, unsigned char* __restrict__ f, long long n) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    p[v] = (int)v;
+    if (f) f[v] = 1;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 namespace {
 int grid_for(long long items, int block, const DeviceInfo& di, int per_sm = 8) {
@@ -286,6 +375,33 @@ cudaError_t launch_split(const long long* off, const int* col, long long n, cons
   hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_HUB);
   flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr);
   count_launches(15);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_disconnected(const int* rep, const int* labels, long long n, int* cnt, unsigned char* flags,
+                                unsigned long long* total, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n, s);
+  cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+  disc_count_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(rep, labels, n, cnt, ctr);
+  disc_flag_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(cnt, n, flags, total);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_lp_init(int* cp, unsigned char* f, long long n, const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  iota_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(cp, f, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_lp_sweep(const long long* off, const int* col, const int* labels, long long n, int* cp,
+                                  unsigned char* fcur, unsigned char* fnext, int prune, Counters* ctr,
+                                  const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  split_lp_kernel<<<16 * di.sm_count, 256, 0, s>>>(off, col, labels, n, cp, fcur, fnext, prune, ctr);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,40 @@ def test_sync_lpa_more_sweeps_and_tolerance_zero(graph, ctx):
     assert np.array_equal(got.cpu().numpy(), want)
 
 
+# ------------------------------------------------- Algorithms 1 and 4 on the GPU
+def test_split_lp_and_disconnected_match_oracle(graph, ctx):
+    rng = np.random.default_rng(13)
+    off, col, _ = dev(graph)
+    lpa_labels, _, _ = O.lpa_sync(graph, 0.05, 20)
+    cases = [lpa_labels, rng.integers(0, max(1, graph.n // 7), graph.n).astype(np.int32),
+             np.zeros(graph.n, dtype=np.int32)]
+    for lab in cases:
+        d_lab = torch.from_numpy(lab).to(DEV)
+        want_split = O.split_bfs(graph, lab)
+        for pruning in (False, True):
+            got, sweeps = ctx.split_lp(off, col, d_lab, pruning=pruning)
+            want_lp, _ = O.split_lp(graph, lab, pruning=pruning)
+            assert np.array_equal(got.cpu().numpy(), want_lp) and np.array_equal(want_lp, want_split)
+            assert sweeps >= 1
+        k, flags = ctx.disconnected(off, col, d_lab, flags=True)
+        want_k, want_flags = O.disconnected(graph, lab)
+        assert k == want_k and np.array_equal(flags.cpu().numpy(), want_flags)
+        split_dev = torch.from_numpy(want_split).to(DEV)
+        assert ctx.disconnected(off, col, split_dev) == 0
+
+
+def test_disconnected_fixture_counts_on_gpu(ctx, gpu_lib):
+    g, _ = load_disconnected40()
+    off, col, _ = dev(g)
+    lab = ctx.lpa(off, col, tolerance=0.05, max_iters=20)
+    k = ctx.disconnected(off, col, lab)
+    assert k == O.disconnected(g, lab.cpu().numpy())[0] and k >= 1
+    with pytest.raises(gpu_lib.GslError):
+        ctx.disconnected(off, col, torch.full((g.n,), g.n, dtype=torch.int32, device=DEV))
+    with pytest.raises(gpu_lib.GslError):
+        ctx.split_lp(off, col, lab, out=lab)
+
+
 # ------------------------------------------------------------------- split
 def test_split_matches_bfs_oracle(graph, ctx, small_ctx):
     rng = np.random.default_rng(11)
@@ -312,6 +346,27 @@ def test_first_sweep_mixed_rows(variants):
         got, st = c.lpa(off, col, stats=True)
         want, t, dn = O.lpa_sync(h, 0.05, 20)
         assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
+
+
+def test_columns_at_any_4_byte_offset(ctx):
+    """The streaming first sweep reads columns 16 bytes at a time after an
+    unaligned head; every start offset gives the same labels."""
+    h = _mixed_rows(seed=3)
+    off = torch.from_numpy(h.offsets).to(DEV)
+    want, t, dn = O.lpa_sync(h, 0.05, 20)
+    big = torch.zeros(h.nnz + 8, dtype=torch.int32, device=DEV)
+    for shift in range(4):
+        col = big[shift:shift + h.nnz]
+        col.copy_(torch.from_numpy(h.cols))
+        got, st = ctx.lpa(off, col, stats=True)
+        assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist(), shift
+        bad = col.clone()
+        bad[h.nnz - 1] = h.n   # an out-of-range column in the scalar tail
+        big2 = torch.zeros_like(big)
+        c2 = big2[shift:shift + h.nnz]
+        c2.copy_(bad)
+        with pytest.raises(Exception):
+            ctx.lpa(off, c2)
 
 
 def test_invalid_inputs_are_rejected(ctx, gpu_lib, variants):

@@ -66,3 +66,19 @@ def test_symmetric_weights():
     d = dict(zip(zip(src.tolist(), g.cols.tolist()), w.tolist()))
     assert all(d[(b, a)] == x for (a, b), x in d.items())
     assert w.min() >= 1 and w.max() <= 9
+
+
+def test_served_request_laws():
+    ps = [I.served_request_params(k) for k in range(4000)]
+    share = sum(p["kind"] == "sbm" for p in ps) / len(ps)
+    assert 0.67 < share < 0.73
+    ns = np.array([p["n"] for p in ps if p["kind"] == "sbm"])
+    assert ns.min() >= 1000 and ns.max() <= 4_194_304
+    # log-uniform: the median is near the geometric mean of the range
+    assert abs(np.log(np.median(ns)) - 0.5 * (np.log(1e3) + np.log(4194304))) < 0.3
+    scales = [p["scale"] for p in ps if p["kind"] == "rmat"]
+    assert min(scales) == 10 and max(scales) == 22
+    assert all(5 <= p["blocks"] <= 200 and 8 <= p["degree"] <= 40 for p in ps if p["kind"] == "sbm")
+    assert I.served_request_params(17) == I.served_request_params(17)
+    g = I.served_request(3)
+    assert g.n == 1 << ps[3]["scale"] if ps[3]["kind"] == "rmat" else g.n == ps[3]["n"]
