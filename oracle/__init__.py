@@ -49,6 +49,8 @@ def configure(lib):
     """Declares the argument and result types of the oracle's C entry points."""
     lib.oracle_sync_sweep.restype = ctypes.c_int64
     lib.oracle_sync_sweep.argtypes = [ctypes.c_int64, i64p, i32p, i32p, i32p, i32p]
+    lib.oracle_sync_sweep_at.restype = ctypes.c_int
+    lib.oracle_sync_sweep_at.argtypes = [ctypes.c_int64, i64p, i32p, i32p, i32p, i64p, ctypes.c_int64, i32p]
     for fn in (lib.oracle_lpa_sync, lib.oracle_lpa_seq):
         fn.restype = ctypes.c_int32
         fn.argtypes = [ctypes.c_int64, i64p, i32p, i32p, i32p, ctypes.c_double, ctypes.c_int32, i32p, i64p]
@@ -97,6 +99,18 @@ def sync_sweep(g, prev, weights="graph"):
     if dn < 0:
         raise MemoryError("oracle_sync_sweep")
     return nxt[:n], int(dn)
+
+
+def sync_sweep_at(g, prev, vertices, weights="graph"):
+    """Eq. 2 for the listed vertices under labels prev (sampled checks)."""
+    n, off, col, w = _graph_args(g, weights)
+    prev = np.ascontiguousarray(prev, dtype=np.int32)
+    sel = np.ascontiguousarray(vertices, dtype=np.int64)
+    out = np.empty(max(sel.shape[0], 1), dtype=np.int32)
+    if _lib().oracle_sync_sweep_at(n, _pp(off, i64p), _pp(col, i32p), _pp(w, i32p), _pp(prev, i32p), _pp(sel, i64p),
+                                   sel.shape[0], _pp(out, i32p)) != 0:
+        raise ValueError("oracle_sync_sweep_at")
+    return out[:sel.shape[0]]
 
 
 def _lpa(fn, g, tau, max_iters, labels_init, weights):

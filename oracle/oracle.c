@@ -13,6 +13,7 @@
  *
  * Contents
  *   oracle_sync_sweep   one Jacobi sweep of Eq. 2 (all vertices, no pruning)
+ *   oracle_sync_sweep_at  the same rule for listed vertices (sampled checks)
  *   oracle_lpa_sync     lpa() of Algorithm 3 with Jacobi sweeps
  *   oracle_lpa_seq      lpa() of Algorithm 3 run by one thread, in place,
  *                       with the processed/unprocessed flags of lpaMove()
@@ -84,6 +85,26 @@ int64_t oracle_sync_sweep(int64_t n, const int64_t* off, const int32_t* col, con
   }
   free(W); free(touched);
   return dn;
+}
+
+/* Eq. 2 for listed vertices only: out[k] = the label oracle_sync_sweep
+ * would give vertex sel[k] under labels prev (the same best_label(), one
+ * vertex at a time), for checking sampled vertices of large graphs.
+ * Returns 0, or -1 (out of memory or a vertex outside [0, n)). */
+int oracle_sync_sweep_at(int64_t n, const int64_t* off, const int32_t* col, const int32_t* w,
+                         const int32_t* prev, const int64_t* sel, int64_t k, int32_t* out) {
+  int64_t maxd = 0;
+  for (int64_t q = 0; q < k; ++q) {
+    if (sel[q] < 0 || sel[q] >= n) return -1;
+    int64_t d = off[sel[q] + 1] - off[sel[q]];
+    if (d > maxd) maxd = d;
+  }
+  int64_t* W = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int32_t* touched = (int32_t*)malloc(sizeof(int32_t) * (size_t)(maxd + 1));
+  if (!W || !touched) { free(W); free(touched); return -1; }
+  for (int64_t q = 0; q < k; ++q) out[q] = best_label(sel[q], off, col, w, prev, W, touched);
+  free(W); free(touched);
+  return 0;
 }
 
 /* lpa() of Algorithm 3 with synchronous sweeps.  labels[] receives C after

@@ -402,3 +402,17 @@ def test_pruned_frontier_reading_is_exact():
             changed = part != cur
             frontier = changed | ((A > 0) & changed[None, :]).any(axis=1)
             cur = part
+
+
+def test_sampled_sweep_equals_full_sweep_on_the_sample():
+    rng = np.random.default_rng(21)
+    for seed in range(4):
+        g = I.rmat(9, 8, seed=seed)
+        w = I.symmetric_weights(g, seed, 5) if seed % 2 else None
+        h = I.Graph(g.offsets, g.cols, w)
+        prev = rng.integers(0, g.n // 8, g.n).astype(np.int32)
+        full, _ = O.sync_sweep(h, prev)
+        sel = rng.permutation(g.n)[:100]
+        assert np.array_equal(O.sync_sweep_at(h, prev, sel), full[sel])
+    with pytest.raises(ValueError):
+        O.sync_sweep_at(h, prev, [g.n])
