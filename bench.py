@@ -285,6 +285,13 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
     batch_ms = e0.elapsed_time(e1) / args.steps
     launches = gsl.kernel_launches() - launches0
+    # per-slot device time of one batch launched directly (outside the timed region)
+    ctx.set_batch_mode(False)
+    ctx.set_profiling(True)
+    ctx.gsllpa_batch(off_d, col_d, vptr, out=out)
+    prof_direct = {p["name"]: round(p["ms"], 3) for p in ctx.profile() if p["ms"] > 0}
+    ctx.set_profiling(False)
+    ctx.set_batch_mode(True)
     # one call per graph, graphs resident, same library
     outs = [torch.empty(o.numel() - 1, dtype=torch.int32, device=dev) for o, _ in solo]
     for (o, c), lab in zip(solo[:64], outs[:64]):
@@ -311,6 +318,7 @@ def run_batched(args):
         "speedup_vs_plain": plain_ms / batch_ms, "labels_identical_to_plain": bool(same),
         "edges_per_s": nnz / (batch_ms * 1e-3), "max_sweeps": int(iters.max()), "mean_sweeps": float(iters.mean()),
         "gpu_launches": launches, "generation_s": gen_s, "clocks": clk.summary(),
+        "profile_direct_ms": prof_direct,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -34,12 +34,15 @@ struct Counters {
   unsigned int pad0;
   unsigned long long cls_scanned[NCLASS];  // CSR entries read per class this sweep
   unsigned long long fast_active;          // vertices settled by the streaming identity sweep
+  unsigned int hub_pieces;                 // pieces of this sweep's class-9 rows
+  unsigned int pad3;
   int err;                      // ERRBIT_* (sticky for the call)
   int pad1;
   // per-graph data filled by the class histogram
   unsigned long long cls_total[NCLASS];  // all vertices per class
   unsigned long long cls_start[NCLASS];  // start of each class's region in the worklist
   long long max_degree;
+  unsigned long long hub_entries;        // entries of all class-9 rows
   int giant;                    // split: root of the most frequent sampled piece
   int pad2;
 };

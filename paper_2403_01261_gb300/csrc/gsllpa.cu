@@ -45,6 +45,20 @@ struct gsl_ctx {
   long long cap_wtab = 0;
   unsigned long long* btab = nullptr;   // block-kernel fallback tables
   long long cap_btab = 0;
+  // class 9 in pieces (hub_kernels.cu)
+  int* hub_piece_start = nullptr;
+  long long* hub_ustart = nullptr;
+  unsigned long long* hub_best = nullptr;
+  unsigned* hub_own = nullptr;
+  unsigned long long* hub_wsum = nullptr;
+  unsigned* hub_used_cnt = nullptr;
+  long long cap_hub_v = 0;              // entries of each of the six per-hub arrays
+  unsigned* hub_used = nullptr;
+  long long cap_hub_used = 0;
+  unsigned long long* hub_tab = nullptr;
+  long long cap_hub_tab = 0;
+  bool hub_ready = false;               // pieces usable for the prepared graph
+  bool hub_dirty = true;                // hub_tab may hold non-empty slots
 
   Counters* ctr = nullptr;         // device
   Counters* ctr_h = nullptr;       // pinned host mirror
@@ -254,6 +268,31 @@ int prepare_graph(gsl_ctx* c, const gsl_csr* g, cudaStream_t s) {
     const long long need = block_grid_size(c->tune, c->di) * 2ll * maxd;
     if (int r = grow(c, c->btab, c->cap_btab, need)) return r;
   }
+  // class 9 (hubs) in pieces: per-hub plan arrays and table regions
+  const long long hubs = (long long)c->ctr_h->cls_total[CLS_HUB];
+  const long long hub_e = (long long)c->ctr_h->hub_entries;
+  c->hub_ready = hubs > 0 && hub_pieces_fit(c->tune) && 2 * hub_e < (1ll << 32);
+  if (c->hub_ready) {
+    const long long old_tab = c->cap_hub_tab;
+    const unsigned long long* old_ptr = c->hub_tab;
+    if (c->cap_hub_v < hubs + 1) {   // the six per-hub arrays share one capacity
+      long long k0 = 0, k1 = 0, k2 = 0, k3 = 0, k4 = 0, k5 = 0;
+      c->cap_hub_v = 0;
+      if (int r = grow(c, c->hub_piece_start, k0, hubs + 1)) return r;
+      if (int r = grow(c, c->hub_ustart, k1, hubs + 1)) return r;
+      if (int r = grow(c, c->hub_best, k2, hubs + 1)) return r;
+      if (int r = grow(c, c->hub_own, k3, hubs + 1)) return r;
+      if (int r = grow(c, c->hub_wsum, k4, hubs + 1)) return r;
+      if (int r = grow(c, c->hub_used_cnt, k5, hubs + 1)) return r;
+      c->cap_hub_v = hubs + 1;
+    }
+    if (int r = grow(c, c->hub_used, c->cap_hub_used, hub_e)) return r;
+    if (int r = grow(c, c->hub_tab, c->cap_hub_tab, 2 * hub_e)) return r;
+    if (c->hub_dirty || c->cap_hub_tab != old_tab || c->hub_tab != old_ptr) {
+      CK(cudaMemsetAsync(c->hub_tab, 0xFF, sizeof(unsigned long long) * (size_t)c->cap_hub_tab, s));
+      c->hub_dirty = false;
+    }
+  }
   return GSL_OK;
 }
 
@@ -352,8 +391,16 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     a.mark = (t > 1 && 2 * dn_prev <= n) ? 1 : 0;
     for (int k = 0; k < NCLASS; ++k) {
       const int pe = prof_begin(c, s);
-      CK(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, s));
-      prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+      if (k == CLS_HUB && c->hub_ready) {
+        HubPlan hp{c->hub_piece_start, c->hub_ustart, c->hub_best, c->hub_own,
+                   c->hub_wsum,        c->hub_used_cnt, c->hub_used, c->hub_tab};
+        c->hub_dirty = true;   // until this sweep is known to have finished cleanly
+        CK(launch_hub_pieces(a, hp, weights != nullptr, async_mode, c->tune, c->di, s));
+        prof_end(c, pe, SL_SWEEP0 + k, s, 3);
+      } else {
+        CK(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, s));
+        prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+      }
     }
     CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -381,6 +428,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
                   4.0 * (double)act_all;
     }
     if (int r = map_err(c, c->ctr_h->err, "lpa")) return r;
+    c->hub_dirty = false;   // every hub's final pass reset the slots its pieces claimed
     const long long dn = (long long)c->ctr_h->dn;
     long long act = (long long)c->ctr_h->fast_active;
     for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
@@ -533,8 +581,12 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
   for (int t = 1; t <= max_iters; ++t) {
     ck(cudaMemsetAsync(c->ctr, 0, offsetof(Counters, err), cs));
     ck(cudaMemsetAsync(c->dn_graph, 0, sizeof(unsigned) * (size_t)num_graphs, cs));
+    // per-slot profiling only when launching directly (not inside a capture)
+    const bool prof = c->prof && c->batch_direct;
+    int pe = prof ? prof_begin(c, cs) : -1;
     ck(launch_bin(OFF(g), n, c->flag[t & 1], t <= 2 ? 1 : 0, c->tune, c->work, c->ctr, c->di, cs, c->gid,
                   c->done, c->stop));
+    if (prof) prof_end(c, pe, SL_BIN, cs, 1);
     a.prev = async_mode ? c->lab[0] : c->lab[(t - 1) & 1];
     a.next = async_mode ? c->lab[0] : c->lab[t & 1];
     a.fnext = c->flag[(t + 1) & 1];
@@ -542,7 +594,11 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
     a.check = t == 1 ? 1 : 0;
     a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
     a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
-    for (int k = 0; k < NCLASS; ++k) ck(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, cs));
+    for (int k = 0; k < NCLASS; ++k) {
+      pe = prof ? prof_begin(c, cs) : -1;
+      ck(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, cs));
+      if (prof) prof_end(c, pe, SL_SWEEP0 + k, cs, 1);
+    }
     ck(launch_graph_update(t, tol, max_iters, c->vptr, num_graphs, c->dn_graph, c->iters, c->done, c->stop, cs));
   }
   const int* bufs[2] = {c->lab[0], c->lab[1]};
@@ -604,7 +660,9 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   if (!c) return GSL_OK;
   DeviceGuard dg(c->device);
   void* dptrs[] = {c->lab[0], c->lab[1], c->flag[0], c->flag[1], c->work, c->parent, c->rank, c->sigma,
-                   c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->ctr, c->sums, c->k_dev,
+                   c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->hub_piece_start,
+                   c->hub_ustart, c->hub_best, c->hub_own, c->hub_wsum, c->hub_used_cnt, c->hub_used, c->hub_tab,
+                   c->ctr, c->sums, c->k_dev,
                    c->st_off, c->st_col, c->st_w, c->st_lab};
   for (void* p : dptrs)
     if (p) cudaFree(p);

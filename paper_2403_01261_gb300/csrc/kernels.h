@@ -94,6 +94,25 @@ cudaError_t launch_batch_final(const int* const* bufs, const int* iters, const i
 cudaError_t launch_localize(const long long* vptr, const int* gid, long long n, int* labels, const DeviceInfo& di,
                             cudaStream_t s);
 
+// hub_kernels.cu: class 9 in pieces.  Arrays sized by the class's vertex
+// total (best, own, wsum, used_cnt: one per hub; piece_start, ustart: one
+// more) and its entry total E (used: E slot indices; tab: 2 E slots, all
+// EMPTY between sweeps; slot indices must stay below 2^32).
+struct HubPlan {
+  int* piece_start;             // first piece of frontier hub i (prefix sums)
+  long long* ustart;            // first entry of hub i's regions (prefix sums of degrees)
+  unsigned long long* best;     // largest packed key over hub i's pieces
+  unsigned* own;                // entries of hub i carrying its own label
+  unsigned long long* wsum;     // weighted degree of hub i (checked when weighted)
+  unsigned* used_cnt;           // table slots claimed for hub i
+  unsigned* used;               // their indices: hub i at used[ustart[i]..]
+  unsigned long long* tab;      // hub i's table at tab[2 ustart[i] .. 2 ustart[i+1])
+};
+// True when a piece always fits the block kernel's shared table.
+bool hub_pieces_fit(const Tuning& t);
+cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weighted, bool async_mode, const Tuning& t,
+                              const DeviceInfo& di, cudaStream_t s);
+
 // split_kernels.cu
 cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels,
                          const int* work, Counters* ctr, int* parent, int* out, const Tuning& t,

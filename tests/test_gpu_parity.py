@@ -348,6 +348,48 @@ def test_first_sweep_mixed_rows(variants):
         assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist()
 
 
+def _giant_hubs(seed=4):
+    """Planted partition of 100,000 vertices plus 5 hubs of 9k-70k random
+    neighbours each: hub rows of several 8192-entry pieces, above the
+    default block-class bound of 32768 for the largest."""
+    rng = np.random.default_rng(seed)
+    base = I.sbm_planted(100_000, 400, 14.0, 3.0, seed=seed)
+    src = np.repeat(np.arange(base.n), np.diff(base.offsets))
+    keep = src < base.cols
+    u, v = [src[keep]], [base.cols[keep]]
+    n = base.n + 5
+    for h, deg in enumerate((70_000, 41_000, 33_000, 20_000, 9_000)):
+        nb = rng.choice(base.n, deg, replace=False)
+        u.append(np.full(nb.shape[0], base.n + h))
+        v.append(nb)
+    u.append(np.array([base.n, base.n + 1]))   # hubs adjacent to each other
+    v.append(np.array([base.n + 2, base.n + 3]))
+    return I.csr_from_pairs(n, np.concatenate(u), np.concatenate(v), name="sbm100k-giant-hubs")
+
+
+@pytest.mark.parametrize("tuning", [None, (1024, 4096), (256, 8192), (32, 48)])
+@pytest.mark.parametrize("w", [False, True])
+def test_hub_pieces_bit_exact(gpu_lib, tuning, w):
+    """Class 9 runs in pieces of 8192 entries aggregated across blocks."""
+    c = gpu_lib.Context(0)
+    if tuning:
+        c.set_tuning(*tuning)
+    for g0 in (_giant_hubs(), I.rmat(17, 24, seed=1)):
+        g = weighted(g0, 5, 3) if w else g0
+        assert np.diff(g.offsets).max() > 8192
+        off, col, wt = dev(g)
+        got, st = c.lpa(off, col, wt, tolerance=0.0, max_iters=6, stats=True)
+        want, t, dn = O.lpa_sync(g, 0.0, 6)
+        assert st["changed"] == dn[:t].tolist() and np.array_equal(got.cpu().numpy(), want), g.name
+        rng = np.random.default_rng(3)
+        prev = rng.integers(0, 50, g.n).astype(np.int32)
+        got1 = c.lpa(off, col, wt, labels_init=torch.from_numpy(prev).to(DEV), tolerance=0.0, max_iters=1)
+        assert np.array_equal(got1.cpu().numpy(), O.sync_sweep(g, prev)[0]), g.name
+        # async: invariants only
+        lab = c.gsllpa(off, col, wt, mode=1).cpu().numpy()
+        assert (lab <= np.arange(g.n)).all() and O.disconnected(g, lab)[0] == 0
+
+
 def test_columns_at_any_4_byte_offset(ctx):
     """The streaming first sweep reads columns 16 bytes at a time after an
     unaligned head; every start offset gives the same labels."""
