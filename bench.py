@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--cache", default=os.environ.get("GSL_BENCH_CACHE", os.path.join(tempfile.gettempdir(),
                                                                                     "gsl_bench_cache")))
     p.add_argument("--profile-json", default="", help="also write the per-slot profile here")
-    p.add_argument("--workload", choices=["rmat", "batched", "served"], default="rmat",
+    p.add_argument("--workload", choices=["rmat", "batched", "served", "compare"], default="rmat",
                    help="rmat: one R-MAT graph (default); batched: many SBM graphs per call vs one call per graph")
     p.add_argument("--graphs", type=int, default=4096, help="graphs in the batched workload")
     p.add_argument("--gen-procs", type=int, default=0, help="host processes generating the batched graphs")
@@ -323,6 +323,65 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
     return 0
 
+# ------------------------------------------------------------ compare mode
+def run_compare(args):
+    """Split on / off (GVE-LPA = LPA alone vs GSL-LPA = LPA + split) and the
+    split techniques (union-find for Algorithm 2, Algorithm 1 with and
+    without pruning) on the synthetic stand-ins: time, modularity and the
+    fraction of disconnected communities (Algorithm 4)."""
+    import numpy as np
+    import torch
+    import inputs as I
+    torch.cuda.set_device(0)
+    import paper_2403_01261_gb300 as gsl
+    dev = torch.device("cuda", 0)
+    graphs = [("sbm10k", I.sbm_planted()), ("lattice-chains", I.lattice_chains())]
+    off_np, col_np = workload_graph(args.scale, args.edge_factor, args.cache, 0, 1)
+    graphs.append((f"rmat{args.scale}", I.Graph(np.asarray(off_np), np.asarray(col_np))))
+    ctx = gsl.Context(0)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(reps):
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return r, statistics.median(ms)
+
+    rows = []
+    for name, g in graphs:
+        off = torch.from_numpy(g.offsets).to(dev)
+        col = torch.from_numpy(g.cols).to(dev)
+        lab, gve_ms = timed(lambda: ctx.lpa(off, col, tolerance=0.05, max_iters=20))
+        out, gsl_ms = timed(lambda: ctx.gsllpa(off, col, tolerance=0.05, max_iters=20))
+        (_, k_uf), uf_ms = timed(lambda: ctx.split(off, col, lab))
+        (_, lp_sweeps), lp_ms = timed(lambda: ctx.split_lp(off, col, lab, pruning=False), reps=1)
+        (_, lpp_sweeps), lpp_ms = timed(lambda: ctx.split_lp(off, col, lab, pruning=True), reps=1)
+        comms = int(torch.unique(lab).numel())
+        disc = ctx.disconnected(off, col, lab)
+        rows.append({
+            "graph": name, "n": g.n, "nnz": g.nnz,
+            "gve_lpa": {"ms": gve_ms, "modularity": ctx.modularity(off, col, lab), "communities": comms,
+                        "disconnected": disc, "disconnected_fraction": disc / max(1, comms)},
+            "gsl_lpa": {"ms": gsl_ms, "modularity": ctx.modularity(off, col, out), "communities": k_uf,
+                        "disconnected": ctx.disconnected(off, col, out)},
+            "split_ms": {"union_find": uf_ms, "sl_lp": lp_ms, "sl_lpp": lpp_ms},
+            "split_sweeps": {"sl_lp": lp_sweeps, "sl_lpp": lpp_sweeps},
+        })
+        del off, col
+    line = {"metric": "GVE-LPA vs GSL-LPA (split on/off) and split techniques on the synthetic stand-ins",
+            "unit": "ms", "n_gpus": 1, "data": "synthetic", "dtype": "int32", "higher_is_better": False,
+            "config": {"workload": "compare", "tolerance": 0.05, "max_iters": 20, "mode": "sync"}, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # -------------------------------------------------------------- served mode
 def _gen_served(ks):
     import inputs as I
@@ -489,6 +548,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "compare":
+        return run_compare(args)
     import numpy as np
     import torch
     rank, world, local = rank_env()

@@ -56,17 +56,36 @@ __device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err) {
   raise_err(err, ERRBIT_TIMEOUT);
 }
 
-constexpr int SPLIT_SAMPLE = 2;   // row entries linked per vertex before the largest piece is known
+constexpr int SPLIT_SAMPLE = 2;   // same-community links per vertex before the largest piece is known
+constexpr int SPLIT_SCAN = 8;     // row entries the sampling pass looks at for them
 
-// Offers entry e of u's row to the union-find if it is an intra-community edge.
-__device__ __forceinline__ void hook_entry(const int* col, const int* labels, int* p, long long n, int u, int cu,
+// Offers entry e of u's row to the union-find if it is an intra-community
+// edge; returns whether it was one.
+__device__ __forceinline__ bool hook_entry(const int* col, const int* labels, int* p, long long n, int u, int cu,
                                            long long e, int* err) {
+  const int j = ld_stream(col + e);
+  if ((unsigned)j >= (unsigned)n) {
+    raise_err(err, ERRBIT_INVALID);
+    return false;
+  }
+  if (j == u || ld_label_ro(labels + j) != cu) return false;
+  uf_unite(p, u, j, err);
+  return true;
+}
+
+// The same after flattening, with ru = u's parent read once per row: when
+// j's parent is ru, u and j already share a tree (trees only merge), so the
+// union is skipped without walking either path.
+__device__ __forceinline__ void hook_entry_flat(const int* col, const int* labels, int* p, long long n, int u,
+                                                int cu, int ru, long long e, int* err) {
   const int j = ld_stream(col + e);
   if ((unsigned)j >= (unsigned)n) {
     raise_err(err, ERRBIT_INVALID);
     return;
   }
-  if (j != u && ld_label_ro(labels + j) == cu) uf_unite(p, u, j, err);
+  if (j == u || ld_label_ro(labels + j) != cu) return;
+  if (__ldcg(p + j) == ru) return;
+  uf_unite(p, u, j, err);
 }
 
 }  // namespace
@@ -76,13 +95,16 @@ __global__ void init_parent_kernel(int* __restrict__ p, long long n) {
     p[v] = (int)v;
 }
 
-// Phase 1: every vertex links with its first SPLIT_SAMPLE row entries.
+// Phase 1: every vertex links with the first SPLIT_SAMPLE same-community
+// neighbours among its first SPLIT_SCAN row entries.
 __global__ void sample_link_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                    const int* __restrict__ labels, int* p, long long n, Counters* ctr) {
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
     const long long s = off[u], e = off[u + 1];
     const int cu = labels[u];
-    for (int k = 0; k < SPLIT_SAMPLE && s + k < e; ++k) hook_entry(col, labels, p, n, (int)u, cu, s + k, &ctr->err);
+    int linked = 0;
+    for (int k = 0; k < SPLIT_SCAN && linked < SPLIT_SAMPLE && s + k < e; ++k)
+      linked += hook_entry(col, labels, p, n, (int)u, cu, s + k, &ctr->err) ? 1 : 0;
   }
 }
 
@@ -143,9 +165,11 @@ __global__ void __launch_bounds__(256) hook_group_kernel(const long long* __rest
   for (long long item = gid; item < (long long)cnt; item += ng) {
     const int u = w[item];
     const long long s = off[u], e = off[u + 1];
-    if (e - s <= SPLIT_SAMPLE || __ldcg(p + u) == giant) continue;
+    if (e - s <= SPLIT_SAMPLE) continue;
+    const int ru = __ldcg(p + u);
+    if (ru == giant) continue;
     const int cu = labels[u];
-    for (long long k = s + SPLIT_SAMPLE + gl; k < e; k += G) hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
+    for (long long k = s + SPLIT_SAMPLE + gl; k < e; k += G) hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err);
   }
 }
 
@@ -156,18 +180,18 @@ __global__ void __launch_bounds__(512) hook_block_kernel(const long long* __rest
   const unsigned cnt = (unsigned)ctr->cls_total[cls];
   const int* w = work + ctr->cls_start[cls];
   const int giant = ctr->giant;
-  __shared__ int s_skip;
+  __shared__ int s_root;
   for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
     const int u = w[item];
     const long long s = off[u], e = off[u + 1];
-    if (threadIdx.x == 0) s_skip = __ldcg(p + u) == giant;
+    if (threadIdx.x == 0) s_root = __ldcg(p + u);
     __syncthreads();
-    const int skip = s_skip;
+    const int ru = s_root;
     __syncthreads();
-    if (skip) continue;
+    if (ru == giant) continue;
     const int cu = labels[u];
     for (long long k = s + SPLIT_SAMPLE + threadIdx.x; k < e; k += blockDim.x)
-      hook_entry(col, labels, p, n, u, cu, k, &ctr->err);
+      hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err);
   }
 }
 
