@@ -360,6 +360,7 @@ def run_compare(args):
         col = torch.from_numpy(g.cols).to(dev)
         lab, gve_ms = timed(lambda: ctx.lpa(off, col, tolerance=0.05, max_iters=20))
         out, gsl_ms = timed(lambda: ctx.gsllpa(off, col, tolerance=0.05, max_iters=20))
+        out_a, async_ms = timed(lambda: ctx.gsllpa(off, col, tolerance=0.05, max_iters=20, mode=1))
         (_, k_uf), uf_ms = timed(lambda: ctx.split(off, col, lab))
         (_, lp_sweeps), lp_ms = timed(lambda: ctx.split_lp(off, col, lab, pruning=False), reps=1)
         (_, lpp_sweeps), lpp_ms = timed(lambda: ctx.split_lp(off, col, lab, pruning=True), reps=1)
@@ -371,6 +372,9 @@ def run_compare(args):
                         "disconnected": disc, "disconnected_fraction": disc / max(1, comms)},
             "gsl_lpa": {"ms": gsl_ms, "modularity": ctx.modularity(off, col, out), "communities": k_uf,
                         "disconnected": ctx.disconnected(off, col, out)},
+            "gsl_lpa_async": {"ms": async_ms, "modularity": ctx.modularity(off, col, out_a),
+                              "communities": int(torch.unique(out_a).numel()),
+                              "disconnected": ctx.disconnected(off, col, out_a)},
             "split_ms": {"union_find": uf_ms, "sl_lp": lp_ms, "sl_lpp": lpp_ms},
             "split_sweeps": {"sl_lp": lp_sweeps, "sl_lpp": lpp_sweeps},
         })

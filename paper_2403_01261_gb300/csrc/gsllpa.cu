@@ -781,6 +781,19 @@ int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t m
   return GSL_OK;
 }
 
+int gsl_ctx_set_block_config(gsl_ctx* c, int32_t threads, int32_t table_slots) {
+  if (!c) return GSL_ERR_INVALID;
+  if (threads != 128 && threads != 256 && threads != 512)
+    return fail(c, GSL_ERR_INVALID, "block threads must be 128, 256 or 512");
+  const long long bytes = (long long)table_slots * 8 + 1024;   // + the kernel's static shared memory
+  if (table_slots < 4 * threads || bytes > c->di.max_smem_optin)
+    return fail(c, GSL_ERR_INVALID, "table_slots must be >= 4 * threads and fit the shared memory of one block");
+  c->tune.blk_block = threads;
+  c->tune.blk_slots = table_slots;
+  c->batch_key.clear();   // the captured batched loop used the old shape
+  return GSL_OK;
+}
+
 int gsl_ctx_set_pregather(gsl_ctx* c, int32_t mode) {
   if (!c) return GSL_ERR_INVALID;
   if (mode < 0 || mode > 2) return fail(c, GSL_ERR_INVALID, "pregather mode must be 0, 1 or 2");

@@ -390,6 +390,22 @@ def test_hub_pieces_bit_exact(gpu_lib, tuning, w):
         assert (lab <= np.arange(g.n)).all() and O.disconnected(g, lab)[0] == 0
 
 
+@pytest.mark.parametrize("shape", [(256, 6144), (128, 1024), (512, 4096), (256, 12288)])
+def test_block_config_does_not_change_results(gpu_lib, shape):
+    c = gpu_lib.Context(0)
+    c.set_block_config(*shape)
+    for g in (_giant_hubs(), I.rmat(16, 24, seed=2)):
+        off, col, _ = dev(g)
+        got, st = c.lpa(off, col, tolerance=0.0, max_iters=5, stats=True)
+        want, t, dn = O.lpa_sync(g, 0.0, 5)
+        assert st["changed"] == dn[:t].tolist() and np.array_equal(got.cpu().numpy(), want), (shape, g.name)
+        assert np.array_equal(c.gsllpa(off, col).cpu().numpy(), O.gsl_lpa(g, 0.05, 20)[0])
+    with pytest.raises(gpu_lib.GslError):
+        c.set_block_config(512, 1024)
+    with pytest.raises(gpu_lib.GslError):
+        c.set_block_config(384, 8192)
+
+
 def test_columns_at_any_4_byte_offset(ctx):
     """The streaming first sweep reads columns 16 bytes at a time after an
     unaligned head; every start offset gives the same labels."""
