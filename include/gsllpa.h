@@ -101,6 +101,16 @@ int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
  * hubs take one block each.  Results do not depend on these values. */
 int gsl_ctx_set_block_config(gsl_ctx* ctx, int32_t threads, int32_t table_slots);
 
+/* Own-label majority pass of the warp and block kernels (degree > 32; the
+ * paper has no counterpart).  Before building a hash table for a row, one
+ * lean pass sums the weight of the entries carrying the vertex's own label;
+ * when it is more than half of the row's weight (the vertex itself
+ * excluded) the own label is Eq. 2's strict argmax and the table is
+ * skipped.  mode 0: never; 1 (default): in sweeps after one that changed
+ * fewer than half of the vertices (batched: from sweep 3); 2: every sweep
+ * after the first.  Labels and statistics do not depend on the mode. */
+int gsl_ctx_set_majority(gsl_ctx* ctx, int32_t mode);
+
 /* Two-phase synchronous sweeps (the paper has no counterpart: it is a GPU
  * scheduling choice).  In a two-phase sweep one edge-parallel pass first
  * gathers the label of every CSR entry's neighbour into a context-owned

@@ -118,6 +118,7 @@ def load():
         lib.gsl_autotune.argtypes = [P, cp, P, i32, i32, ctypes.POINTER(TuneResult), P]
         lib.gsl_ctx_set_pregather.argtypes = [P, i32]
         lib.gsl_ctx_set_block_config.argtypes = [P, i32, i32]
+        lib.gsl_ctx_set_majority.argtypes = [P, i32]
         lib.gsl_split_lp.argtypes = [P, cp, P, P, i32, ctypes.POINTER(i32), P]
         lib.gsl_disconnected.argtypes = [P, cp, P, P, ctypes.POINTER(i64), P]
         lib.gsl_lpa.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
@@ -221,6 +222,10 @@ class Context:
 
     def set_block_config(self, threads: int, table_slots: int):
         self._raise(self._lib.gsl_ctx_set_block_config(self._h, int(threads), int(table_slots)))
+
+    def set_majority(self, mode: int):
+        """0: never, 1: once labels settle (default), 2: every sweep after the first."""
+        self._raise(self._lib.gsl_ctx_set_majority(self._h, int(mode)))
 
     def set_pregather(self, mode: int):
         """0: never (default), 1: when the frontier is large, 2: every eligible sweep."""

@@ -389,6 +389,10 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     // one that changed more than half of the vertices is run on all
     // vertices: marking would select nearly everything anyway.
     a.mark = (t > 1 && 2 * dn_prev <= n) ? 1 : 0;
+    // once fewer than half of the vertices changed, most rows keep a
+    // majority of their own label: test that before building a table
+    a.majority = (!a.ident && !a.check &&
+                  (c->tune.majority == 2 || (c->tune.majority == 1 && t > 1 && 2 * dn_prev < n))) ? 1 : 0;
     for (int k = 0; k < NCLASS; ++k) {
       const int pe = prof_begin(c, s);
       if (k == CLS_HUB && c->hub_ready) {
@@ -593,6 +597,7 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
     a.ident = (!async_mode && t == 1) ? 1 : 0;
     a.check = t == 1 ? 1 : 0;
     a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
+    a.majority = (!a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3))) ? 1 : 0;
     a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
     for (int k = 0; k < NCLASS; ++k) {
       pe = prof ? prof_begin(c, cs) : -1;
@@ -791,6 +796,14 @@ int gsl_ctx_set_block_config(gsl_ctx* c, int32_t threads, int32_t table_slots) {
   c->tune.blk_block = threads;
   c->tune.blk_slots = table_slots;
   c->batch_key.clear();   // the captured batched loop used the old shape
+  return GSL_OK;
+}
+
+int gsl_ctx_set_majority(gsl_ctx* c, int32_t mode) {
+  if (!c) return GSL_ERR_INVALID;
+  if (mode < 0 || mode > 2) return fail(c, GSL_ERR_INVALID, "majority mode must be 0, 1 or 2");
+  c->tune.majority = mode;
+  c->batch_key.clear();
   return GSL_OK;
 }
 

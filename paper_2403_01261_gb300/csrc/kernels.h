@@ -30,6 +30,7 @@ struct SweepArgs {
   int ident;                 // prev is the identity labelling (not read)
   int check;                 // validate weights and weighted degrees
   int mark;                  // mark neighbours of changed vertices in fnext
+  int majority;              // test for an own-label majority before building a table
   const int* lg;             // sync mode: labels gathered per entry, lg[e] = prev[col[e]] (null: gather)
 };
 
@@ -42,6 +43,7 @@ struct Tuning {
   int warp_block = 256;      // threads per block of the warp kernel
   int blk_block = 512;       // threads per block of the block kernel
   int pregather = 0;         // two-phase sweeps: 0 never, 1 when the frontier is large, 2 always
+  int majority = 1;          // own-label majority pass: 0 never, 1 once labels settle, 2 always
 };
 
 // Degree bounds of the classes (see common.cuh).

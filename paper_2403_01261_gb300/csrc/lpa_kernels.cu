@@ -363,6 +363,19 @@ __global__ void __launch_bounds__(256, 3) sweep_warp_kernel(SweepArgs a, int cls
     unsigned long long best = 0, wsum = 0;
     bool done = false;
     if (a.ident && !ASYNC) done = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, pol, best, wsum));
+    if (!done && a.majority) {   // an own-label majority settles the row without a table
+      unsigned ow = 0, tw = 0;
+      own_weight_pass<WEIGHTED, ASYNC>(a, v, old, cp, wp, a.lg ? a.lg + s : nullptr, d, lane, 32, pol, ow, tw);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        ow += __shfl_xor_sync(FULL, ow, o);
+        tw += __shfl_xor_sync(FULL, tw, o);
+      }
+      if (2ull * ow > (unsigned long long)tw) {
+        done = true;
+        best = 0;   // nl = old below
+      }
+    }
     if (!done) {
       best = 0;
       wsum = 0;
@@ -464,7 +477,32 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
         __syncthreads();
       }
     }
-    if (!sorted) {
+    bool settled = false;
+    if (!sorted && a.majority) {
+      // every row of the launch takes this pass and its barrier, so the
+      // per-warp slots of row parity `par` are no longer read by any thread
+      // when the row after next writes them
+      unsigned ow = 0, tw = 0;
+      own_weight_pass<WEIGHTED, ASYNC>(a, v, old, cp, wp, lp, d, threadIdx.x, blockDim.x, pol, ow, tw);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        ow += __shfl_xor_sync(FULL, ow, o);
+        tw += __shfl_xor_sync(FULL, tw, o);
+      }
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      if (lane == 0) {
+        sh.maj[par][0][wid] = ow;
+        sh.maj[par][1][wid] = tw;
+      }
+      __syncthreads();
+      unsigned long long o_all = 0, t_all = 0;
+      for (int k = 0; k < nw; ++k) {
+        o_all += sh.maj[par][0][k];
+        t_all += sh.maj[par][1][k];
+      }
+      settled = 2 * o_all > t_all;
+    }
+    if (!sorted && !settled) {
       const unsigned want = 2u * (unsigned)d;
       int ovf = 1;
       if (!(gthresh > 0 && d > gthresh)) {
@@ -475,8 +513,8 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
       }
       if (ovf) block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
     }
-    unsigned long long b = sh.best[par];
-    const unsigned own_sum = sh.own[par];
+    unsigned long long b = settled ? 0ull : sh.best[par];
+    const unsigned own_sum = settled ? 0u : sh.own[par];
     if (own_sum) {
       const unsigned long long k = pack_key(own_sum, old);
       b = k > b ? k : b;
@@ -484,7 +522,7 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
     const int nl = b ? (int)~(unsigned)b : old;
     const bool changed = nl != old;
     if (threadIdx.x == 0) {
-      if (WEIGHTED && a.check && sh.wsum[par] >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+      if (WEIGHTED && a.check && !settled && sh.wsum[par] >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
       store_label<ASYNC>(a, v, nl, changed);
       if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;

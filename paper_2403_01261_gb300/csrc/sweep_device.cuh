@@ -148,7 +148,46 @@ struct BlockRowShared {
   unsigned long long best[2], wsum[2];
   unsigned used[2], own[2];
   int ovf[2];
+  unsigned maj[2][2][32];   // per warp: (own-label weight, total weight) of the majority pass
 };
+
+// Own-label majority pass: one lean pass over the row sums, per thread, the
+// weight of the entries that carry the vertex's own label and the weight of
+// all entries (the vertex itself excluded).  When the own label holds more
+// than half of the total it is Eq. 2's strict argmax and the row needs no
+// table.  Thread tid of nthreads takes 32-entry chunks as block_row does,
+// with the columns of the next round requested before this round's labels
+// are compared.
+template <bool WEIGHTED, bool ASYNC>
+__device__ __forceinline__ void own_weight_pass(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
+                                                const int* lp, int d, int tid, int nthreads, const Pol& pol,
+                                                unsigned& own_w, unsigned& tot_w) {
+  const int lane = tid & 31, wid = tid >> 5, nw = nthreads >> 5;
+  const int step = nw * 128;
+  const int cb = wid * 32 + lane, cu = nw * 32;
+  int jn[4], wn[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, cb + u * cu, pol, jn[u], wn[u]);
+  for (int r0 = 0; r0 < d; r0 += step) {
+    int l[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      l[u] = entry_label<ASYNC>(a, lp, r0 + cb + u * cu, jn[u], v, pol);
+      w[u] = wn[u];
+    }
+    if (r0 + step < d) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, r0 + step + cb + u * cu, pol, jn[u], wn[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (l[u] >= 0) {
+        tot_w += (unsigned)w[u];
+        if (l[u] == own) own_w += (unsigned)w[u];
+      }
+    }
+  }
+}
 
 // Reduces the block's per-thread partial results into sh[par]; the caller
 // synchronises before reading them.

@@ -56,10 +56,18 @@ def variants(ctx, small_ctx, gpu_lib):
     small_pre.set_pregather(2)
     never = gpu_lib.Context(0)
     never.set_pregather(0)
-    return {"default": ctx, "small": small_ctx, "pre": pre, "small_pre": small_pre, "never": never}
+    never.set_majority(0)
+    maj = gpu_lib.Context(0)   # own-label majority pass in every sweep, tiny thresholds
+    maj.set_tuning(32, 48)
+    maj.set_majority(2)
+    maj_pre = gpu_lib.Context(0)
+    maj_pre.set_majority(2)
+    maj_pre.set_pregather(2)
+    return {"default": ctx, "small": small_ctx, "pre": pre, "small_pre": small_pre, "never": never, "maj": maj,
+            "maj_pre": maj_pre}
 
 
-VARIANTS = ["default", "small", "pre", "small_pre", "never"]
+VARIANTS = ["default", "small", "pre", "small_pre", "never", "maj", "maj_pre"]
 
 GRAPHS = {
     "two_k5": lambda: I.two_cliques_bridge(5),
@@ -374,6 +382,7 @@ def test_hub_pieces_bit_exact(gpu_lib, tuning, w):
     c = gpu_lib.Context(0)
     if tuning:
         c.set_tuning(*tuning)
+        c.set_majority(2)
     for g0 in (_giant_hubs(), I.rmat(17, 24, seed=1)):
         g = weighted(g0, 5, 3) if w else g0
         assert np.diff(g.offsets).max() > 8192
