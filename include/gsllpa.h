@@ -101,14 +101,15 @@ int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
  * hubs take one block each.  Results do not depend on these values. */
 int gsl_ctx_set_block_config(gsl_ctx* ctx, int32_t threads, int32_t table_slots);
 
-/* Own-label majority pass of the warp and block kernels (degree > 32; the
- * paper has no counterpart).  Before building a hash table for a row, one
- * lean pass sums the weight of the entries carrying the vertex's own label;
- * when it is more than half of the row's weight (the vertex itself
- * excluded) the own label is Eq. 2's strict argmax and the table is
- * skipped.  mode 0: never; 1 (default): in sweeps after one that changed
- * fewer than half of the vertices (batched: from sweep 3); 2: every sweep
- * after the first.  Labels and statistics do not depend on the mode. */
+/* Own-label majority filter for rows of the two longest table classes
+ * (degree above 256 up to blk_max; the paper has no counterpart).  Before
+ * their hash tables are built, one lean warp-per-row pass sums the weight
+ * of a row's entries carrying the vertex's own label; when it is more than
+ * half of the row's weight (the vertex itself excluded) the own label is
+ * Eq. 2's strict argmax and the row is done.  mode 0: never; 1 (default):
+ * from sweep 3 on (sweep 2 reads the nearly all-distinct labels of sweep 1);
+ * 2: every sweep after the first.  Labels and statistics do not depend on
+ * the mode. */
 int gsl_ctx_set_majority(gsl_ctx* ctx, int32_t mode);
 
 /* Two-phase synchronous sweeps (the paper has no counterpart: it is a GPU
@@ -175,6 +176,25 @@ int gsl_autotune(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, int32_t
 int gsl_lpa(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, const int32_t* labels_init,
             double tolerance, int32_t max_iters, int32_t mode, int32_t* labels_out,
             gsl_stats* stats, void* stream);
+
+/* Float weights at the paper's precision (Section 4.1: 32-bit float edge
+ * weights, 64-bit float label sums).  Same arguments and behaviour as
+ * gsl_lpa / gsl_gsllpa / gsl_modularity except that `weights` is a device
+ * float[nnz] (required when nnz > 0) whose every value must be finite and
+ * > 0 (else GSL_ERR_INVALID).  The label with the largest float64 sum
+ * wins, ties to the smallest label.  Sums of non-integer weights depend on
+ * the order of the additions, which is not fixed on the GPU, so labels are
+ * not guaranteed bit-identical to a sequential evaluation where two sums
+ * agree to rounding; they are whenever every partial sum is exact in
+ * float64 (for instance small integers or multiples of 1/8).  Modularity is
+ * formed from float64 sums. */
+int gsl_lpa_f32(gsl_ctx* ctx, const gsl_csr* g, const float* weights, const int32_t* labels_init,
+                double tolerance, int32_t max_iters, int32_t mode, int32_t* labels_out, gsl_stats* stats,
+                void* stream);
+int gsl_gsllpa_f32(gsl_ctx* ctx, const gsl_csr* g, const float* weights, double tolerance, int32_t max_iters,
+                   int32_t mode, int32_t* labels_out, gsl_stats* stats, void* stream);
+int gsl_modularity_f32(gsl_ctx* ctx, const gsl_csr* g, const float* weights, const int32_t* labels,
+                       double* q_out, void* stream);
 
 /* Split last: splitDisconnectedBfs() of Algorithm 2.  labels_out[v] becomes
  * the smallest vertex id of the connected piece of v's community that holds

@@ -49,6 +49,14 @@ def configure(lib):
     """Declares the argument and result types of the oracle's C entry points."""
     lib.oracle_sync_sweep.restype = ctypes.c_int64
     lib.oracle_sync_sweep.argtypes = [ctypes.c_int64, i64p, i32p, i32p, i32p, i32p]
+    f32p = ctypes.POINTER(ctypes.c_float)
+    lib.oracle_sync_sweep_f32.restype = ctypes.c_int64
+    lib.oracle_sync_sweep_f32.argtypes = [ctypes.c_int64, i64p, i32p, f32p, i32p, i32p]
+    lib.oracle_lpa_sync_f32.restype = ctypes.c_int32
+    lib.oracle_lpa_sync_f32.argtypes = [ctypes.c_int64, i64p, i32p, f32p, i32p, ctypes.c_double, ctypes.c_int32,
+                                        i32p, i64p]
+    lib.oracle_modularity_f64.restype = ctypes.c_int
+    lib.oracle_modularity_f64.argtypes = [ctypes.c_int64, i64p, i32p, f32p, i32p, ctypes.POINTER(ctypes.c_double)]
     lib.oracle_sync_sweep_at.restype = ctypes.c_int
     lib.oracle_sync_sweep_at.argtypes = [ctypes.c_int64, i64p, i32p, i32p, i32p, i64p, ctypes.c_int64, i32p]
     for fn in (lib.oracle_lpa_sync, lib.oracle_lpa_seq):
@@ -99,6 +107,56 @@ def sync_sweep(g, prev, weights="graph"):
     if dn < 0:
         raise MemoryError("oracle_sync_sweep")
     return nxt[:n], int(dn)
+
+
+def _f32(g, wf):
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    col = np.ascontiguousarray(g.cols, dtype=np.int32)
+    w = np.ascontiguousarray(wf, dtype=np.float32)
+    assert w.shape[0] == col.shape[0]
+    return off.shape[0] - 1, off, col, w
+
+
+def sync_sweep_f32(g, wf, prev):
+    """Eq. 2 with float32 weights wf[nnz] and float64 sums -> (next, dN)."""
+    n, off, col, w = _f32(g, wf)
+    prev = np.ascontiguousarray(prev, dtype=np.int32)
+    nxt = np.empty(max(n, 1), dtype=np.int32)
+    dn = _lib().oracle_sync_sweep_f32(n, _pp(off, i64p), _pp(col, i32p), _pp(w, ctypes.POINTER(ctypes.c_float)),
+                                      _pp(prev, i32p), _pp(nxt, i32p))
+    if dn < 0:
+        raise ValueError("oracle_sync_sweep_f32: bad weight or out of memory")
+    return nxt[:n], int(dn)
+
+
+def lpa_sync_f32(g, wf, tau=0.05, max_iters=20, labels_init=None):
+    """lpa() of Algorithm 3, Jacobi sweeps, float32 weights -> (labels, sweeps, dN)."""
+    n, off, col, w = _f32(g, wf)
+    lab = np.empty(max(n, 1), dtype=np.int32)
+    dn = np.zeros(max(max_iters, 1), dtype=np.int64)
+    init = None if labels_init is None else np.ascontiguousarray(labels_init, dtype=np.int32)
+    t = _lib().oracle_lpa_sync_f32(n, _pp(off, i64p), _pp(col, i32p), _pp(w, ctypes.POINTER(ctypes.c_float)),
+                                   _pp(init, i32p), float(tau), int(max_iters), _pp(lab, i32p), _pp(dn, i64p))
+    if t < 0:
+        raise ValueError("oracle_lpa_sync_f32: bad weight or out of memory")
+    return lab[:n], int(t), dn[:t]
+
+
+def modularity_f64(g, wf, labels):
+    """Eq. 1 with float32 weights and float64 sums."""
+    n, off, col, w = _f32(g, wf)
+    C = np.ascontiguousarray(labels, dtype=np.int32)
+    q = ctypes.c_double()
+    if _lib().oracle_modularity_f64(n, _pp(off, i64p), _pp(col, i32p), _pp(w, ctypes.POINTER(ctypes.c_float)),
+                                    _pp(C, i32p), ctypes.byref(q)) != 0:
+        raise ValueError("oracle_modularity_f64")
+    return q.value
+
+
+def gsl_lpa_f32(g, wf, tau=0.05, max_iters=20):
+    """GSL-LPA with float32 weights: lpa_sync_f32 then splitDisconnectedBfs()."""
+    lab, t, dn = lpa_sync_f32(g, wf, tau, max_iters)
+    return split_bfs(g, lab), t, dn
 
 
 def sync_sweep_at(g, prev, vertices, weights="graph"):

@@ -21,6 +21,7 @@
  *   oracle_split_lp     splitDisconnectedLp() of Algorithm 1 (SL-LP / SL-LPP)
  *   oracle_modularity   Eq. 1 (second form), exact integer parts
  *   oracle_disconnected disconnectedCommunities() of Algorithm 4
+ *   oracle_*_f32 / _f64 the same with float weights and double sums
  *
  * Readings taken where the paper is silent (all also listed in the design
  * notes):
@@ -267,6 +268,99 @@ int oracle_modularity(int64_t n, const int64_t* off, const int32_t* col, const i
   if (two_m == 0) { *q = 0.0; return 0; }
   double dm = (double)two_m;
   *q = (double)s1 / dm - (double)s2 / (dm * dm);
+  return 0;
+}
+
+/* ------------------------------------------------ fp32 weights, fp64 sums */
+/* The paper's own precision (Section 4.1): 32-bit float edge weights and
+ * 64-bit float hashtable values.  best_label_f is Eq. 2 with every label's
+ * sum accumulated in double in row order; equal sums go to the smallest
+ * label.  Weights must be finite and > 0 (a zero sum then means "not seen"). */
+static int32_t best_label_f(int64_t i, const int64_t* off, const int32_t* col, const float* w, const int32_t* C,
+                            double* W, int32_t* touched) {
+  int64_t nt = 0;
+  for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+    int32_t j = col[e];
+    if (j == i) continue;
+    int32_t c = C[j];
+    if (W[c] == 0.0) touched[nt++] = c;
+    W[c] += (double)w[e];
+  }
+  if (nt == 0) return C[i];
+  int32_t best = touched[0];
+  double bestw = W[best];
+  for (int64_t k = 1; k < nt; ++k) {
+    int32_t c = touched[k];
+    if (W[c] > bestw || (W[c] == bestw && c < best)) { best = c; bestw = W[c]; }
+  }
+  for (int64_t k = 0; k < nt; ++k) W[touched[k]] = 0.0;
+  return best;
+}
+
+/* One Jacobi sweep with float weights; returns dN, or -1 (out of memory or
+ * a weight that is not finite and positive). */
+int64_t oracle_sync_sweep_f32(int64_t n, const int64_t* off, const int32_t* col, const float* w,
+                              const int32_t* prev, int32_t* next) {
+  for (int64_t e = 0; e < (n > 0 ? off[n] : 0); ++e)
+    if (!(w[e] > 0.0f) || w[e] != w[e] || w[e] > 3.4e38f) return -1;
+  double* W = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  int32_t* touched = (int32_t*)malloc(sizeof(int32_t) * (size_t)(max_degree(n, off) + 1));
+  if (!W || !touched) { free(W); free(touched); return -1; }
+  int64_t dn = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    next[i] = best_label_f(i, off, col, w, prev, W, touched);
+    if (next[i] != prev[i]) ++dn;
+  }
+  free(W); free(touched);
+  return dn;
+}
+
+/* lpa() of Algorithm 3 with synchronous sweeps and float weights (the stop
+ * rule as in oracle_lpa_sync). */
+int32_t oracle_lpa_sync_f32(int64_t n, const int64_t* off, const int32_t* col, const float* w,
+                            const int32_t* labels_init, double tau, int32_t max_iters,
+                            int32_t* labels, int64_t* dn_per_sweep) {
+  for (int64_t i = 0; i < n; ++i) labels[i] = labels_init ? labels_init[i] : (int32_t)i;
+  if (n == 0) return 0;
+  int32_t* next = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!next) return -1;
+  int32_t t = 0;
+  while (t < max_iters) {
+    int64_t dn = oracle_sync_sweep_f32(n, off, col, w, labels, next);
+    if (dn < 0) { free(next); return -1; }
+    memcpy(labels, next, sizeof(int32_t) * (size_t)n);
+    if (dn_per_sweep) dn_per_sweep[t] = dn;
+    ++t;
+    if ((double)dn / (double)n <= tau) break;
+  }
+  free(next);
+  return t;
+}
+
+/* Eq. 1 (second form) with float weights, every sum in double:
+ * Q = S1/2m - S2/(2m)^2 with 2m = sum of entry weights, S1 = weight of
+ * entries inside communities, S2 = sum over communities of Sigma_c^2.
+ * Returns 0, or -1 (out of memory or a label outside [0, n)). */
+int oracle_modularity_f64(int64_t n, const int64_t* off, const int32_t* col, const float* w, const int32_t* C,
+                          double* q) {
+  double* Sigma = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!Sigma) return -1;
+  for (int64_t i = 0; i < n; ++i) if (C[i] < 0 || C[i] >= n) { free(Sigma); return -1; }
+  double two_m = 0.0, s1 = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double K = 0.0;
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+      double we = (double)w[e];
+      K += we;
+      if (C[col[e]] == C[i]) s1 += we;
+    }
+    two_m += K;
+    Sigma[C[i]] += K;
+  }
+  double s2 = 0.0;
+  for (int64_t c = 0; c < n; ++c) s2 += Sigma[c] * Sigma[c];
+  free(Sigma);
+  *q = two_m == 0.0 ? 0.0 : s1 / two_m - s2 / (two_m * two_m);
   return 0;
 }
 

@@ -119,6 +119,9 @@ def load():
         lib.gsl_ctx_set_pregather.argtypes = [P, i32]
         lib.gsl_ctx_set_block_config.argtypes = [P, i32, i32]
         lib.gsl_ctx_set_majority.argtypes = [P, i32]
+        lib.gsl_lpa_f32.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
+        lib.gsl_gsllpa_f32.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
+        lib.gsl_modularity_f32.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
         lib.gsl_split_lp.argtypes = [P, cp, P, P, i32, ctypes.POINTER(i32), P]
         lib.gsl_disconnected.argtypes = [P, cp, P, P, ctypes.POINTER(i64), P]
         lib.gsl_lpa.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
@@ -260,6 +263,46 @@ class Context:
                                int(max_iters), int(mode), _ptr(out), ctypes.byref(st), _stream(stream))
         self._raise(rc)
         return (out, st.as_dict()) if stats else out
+
+    def _check_f32(self, cols, weights):
+        import torch
+        if (weights is None or weights.dtype != torch.float32 or not weights.is_cuda or not weights.is_contiguous()
+                or weights.numel() != cols.numel()):
+            raise TypeError("weights must be a contiguous float32 CUDA tensor with one entry per column")
+
+    def lpa_f32(self, offsets, cols, weights, labels_init=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC,
+                out=None, stream=None, stats=False):
+        """LPA with float32 weights and float64 sums (the paper's precision)."""
+        import torch
+        g = _check_graph(offsets, cols)
+        self._check_f32(cols, weights)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        st = Stats()
+        self._raise(self._lib.gsl_lpa_f32(self._h, ctypes.byref(g), _ptr(weights), _ptr(labels_init),
+                                          float(tolerance), int(max_iters), int(mode), _ptr(out), ctypes.byref(st),
+                                          _stream(stream)))
+        return (out, st.as_dict()) if stats else out
+
+    def gsllpa_f32(self, offsets, cols, weights, tolerance=0.05, max_iters=20, mode=MODE_SYNC, out=None,
+                   stream=None, stats=False):
+        import torch
+        g = _check_graph(offsets, cols)
+        self._check_f32(cols, weights)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        st = Stats()
+        self._raise(self._lib.gsl_gsllpa_f32(self._h, ctypes.byref(g), _ptr(weights), float(tolerance),
+                                             int(max_iters), int(mode), _ptr(out), ctypes.byref(st), _stream(stream)))
+        return (out, st.as_dict()) if stats else out
+
+    def modularity_f32(self, offsets, cols, labels, weights, stream=None):
+        g = _check_graph(offsets, cols)
+        self._check_f32(cols, weights)
+        q = ctypes.c_double()
+        self._raise(self._lib.gsl_modularity_f32(self._h, ctypes.byref(g), _ptr(weights), _ptr(labels),
+                                                 ctypes.byref(q), _stream(stream)))
+        return q.value
 
     def split(self, offsets, cols, labels, renumber=False, out=None, stream=None):
         import torch

@@ -36,6 +36,7 @@ struct Counters {
   unsigned long long fast_active;          // vertices settled by the streaming identity sweep
   unsigned int hub_pieces;                 // pieces of this sweep's class-9 rows
   unsigned int pad3;
+  unsigned int uns_count[NCLASS];          // majority filter: rows left for the table kernels
   int err;                      // ERRBIT_* (sticky for the call)
   int pad1;
   // per-graph data filled by the class histogram

@@ -1,0 +1,337 @@
+// float_kernels.cu -- LPA sweeps and modularity at the paper's precision:
+// float32 edge weights, float64 label sums (Section 4.1).
+//
+// Eq. 2 picks the label with the largest float64 sum, ties to the smallest
+// label.  Unlike the int32 path, sums of non-integer weights depend on the
+// order of the additions, so labels can differ from a sequential evaluation
+// where two sums agree to rounding; when every partial sum is exact in
+// float64 (small integers, dyadic fractions) the result is exact.
+//   d <= 32   lane groups: equal labels found with __match_any_sync; each
+//             lane sums its group's weights in lane order (row order); the
+//             argmax is a shuffle reduction over (sum, label);
+//   d > 32    one block per row: a table of (label, float64 sum) slots in
+//             shared memory (global memory when 2 d exceeds it); labels are
+//             merged per 32-entry chunk first; after all adds the table is
+//             scanned for the argmax.
+#include <cfloat>
+
+#include "sweep_device.cuh"
+
+namespace gsl {
+
+namespace {
+
+constexpr unsigned EMPTY32 = 0xFFFFFFFFu;
+constexpr int F_BLOCK = 256;            // threads per block of the table kernel
+constexpr unsigned F_TABLE_SLOTS = 8192;  // shared-memory slots per block (12 bytes each)
+constexpr int F_BLOCKS_PER_SM = 2;
+
+// (s1, l1) beats (s2, l2): larger sum, then smaller label; label -1 = none.
+__device__ __forceinline__ bool fbetter(double s1, int l1, double s2, int l2) {
+  if (l1 < 0) return false;
+  if (l2 < 0) return true;
+  return s1 > s2 || (s1 == s2 && l1 < l2);
+}
+
+template <int WIDTH>
+__device__ __forceinline__ void fbest_reduce(double& s, int& l) {
+#pragma unroll
+  for (int o = WIDTH / 2; o >= 1; o >>= 1) {
+    const double s2 = __shfl_xor_sync(FULL, s, o, WIDTH);
+    const int l2 = __shfl_xor_sync(FULL, l, o, WIDTH);
+    if (fbetter(s2, l2, s, l)) {
+      s = s2;
+      l = l2;
+    }
+  }
+}
+
+// Entry e of a row: neighbour j (-1 past the end or out of range) and its
+// float weight; with `check`, a weight that is not finite and positive is
+// reported.
+__device__ __forceinline__ void load_entry_f(const SweepArgs& a, const int* cp, const float* wp, int d, int e,
+                                             const Pol& pol, int& j, float& w) {
+  j = -1;
+  w = 0.f;
+  if (e < d) {
+    j = ld_stream(cp + e, pol.stream);
+    w = __ldg(wp + e);
+    if ((unsigned)j >= (unsigned)a.n || (a.check && !(w > 0.f && w <= FLT_MAX))) {
+      raise_err(&a.ctr->err, ERRBIT_INVALID);
+      j = -1;
+    }
+  }
+}
+
+// Adds c to label lbl's sum in an open-addressing table of cap slots.
+template <bool GLOBAL>
+__device__ __forceinline__ void fslot_add(unsigned* keys, double* vals, unsigned cap, unsigned lbl, double c,
+                                          int* err) {
+  unsigned h = __umulhi(hash32(lbl), cap);
+  for (int p = 0; p < PROBE_CAP; ++p) {
+    unsigned k = GLOBAL ? __ldcg(keys + h) : *(volatile unsigned*)(keys + h);
+    if (k == EMPTY32) k = atomicCAS(keys + h, EMPTY32, lbl);
+    if (k == EMPTY32 || k == lbl) {
+      atomicAdd(vals + h, c);
+      return;
+    }
+    if (++h == cap) h = 0;
+  }
+  raise_err(err, ERRBIT_TIMEOUT);
+}
+
+}  // namespace
+
+template <int G, bool ASYNC>
+__global__ void __launch_bounds__(256) sweep_f_group_kernel(SweepArgs a, const float* __restrict__ wf, int cls) {
+  const unsigned cnt = a.ctr->cls_count[cls];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const Pol pol = make_pol();
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const int gbase = lane & ~(G - 1);
+  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
+  constexpr int PER_WARP = 32 / G;
+  const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_dn = 0, my_scan = 0;
+  for (long long wb = warp_id * PER_WARP; wb < (long long)cnt; wb += nwarps * PER_WARP) {
+    const long long item = wb + lane / G;
+    const bool has = item < (long long)cnt;
+    int v = 0, d = 0;
+    long long s = 0;
+    if (has) {
+      v = work[item];
+      s = a.off[v];
+      d = (int)(a.off[v + 1] - s);
+    }
+    int j;
+    float w;
+    load_entry_f(a, a.col + s, wf + s, d, gl, pol, j, w);
+    const int lbl = entry_label<ASYNC>(a, nullptr, gl, j, v, pol);
+    const unsigned m = __match_any_sync(FULL, lbl) & gmask;
+    double sum = 0.0;   // this lane's label, its group's weights in lane order
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const double x = (double)__shfl_sync(FULL, w, gbase + k);
+      if ((m >> (gbase + k)) & 1u) sum += x;
+    }
+    double bs = sum;
+    int bl = lbl;
+    fbest_reduce<G>(bs, bl);
+    bool changed = false;
+    if (has && gl == 0) {
+      const int old = own_label<ASYNC>(a, v);
+      const int nl = bl >= 0 ? bl : old;
+      changed = nl != old;
+      store_label<ASYNC>(a, v, nl, changed);
+      if (changed) count_graph_change(a, v);
+      my_scan += (unsigned long long)d;
+      my_dn += changed ? 1ull : 0ull;
+    }
+    if (a.mark) {
+      const unsigned chm = __ballot_sync(FULL, changed);
+      if ((chm >> gbase) & 1u) {
+        if (j >= 0) a.fnext[j] = 1;
+        if (!ASYNC && gl == 0) a.fnext[v] = 1;
+      }
+    }
+  }
+  flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// One block per row of classes 6..9; `tb` table slots in shared memory,
+// global regions of 2 * (largest degree) slots per block otherwise.
+template <bool ASYNC>
+__global__ void __launch_bounds__(F_BLOCK) sweep_f_block_kernel(SweepArgs a, const float* __restrict__ wf, int cls,
+                                                               unsigned tb, unsigned* gkeys, double* gvals,
+                                                               long long region) {
+  extern __shared__ unsigned char smem_f[];
+  double* svals = reinterpret_cast<double*>(smem_f);
+  unsigned* skeys = reinterpret_cast<unsigned*>(smem_f + sizeof(double) * tb);
+  __shared__ double s_bs[F_BLOCK / 32];
+  __shared__ int s_bl[F_BLOCK / 32];
+  __shared__ int s_changed;
+  const unsigned cnt = a.ctr->cls_count[cls];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const Pol pol = make_pol();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long my_dn = 0, my_scan = 0;
+  for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
+    const int v = work[item];
+    const long long s = a.off[v];
+    const int d = (int)(a.off[v + 1] - s);
+    const bool global = 2u * (unsigned)d > tb;
+    const unsigned cap = 2u * (unsigned)d;
+    unsigned* keys = global ? gkeys + (long long)blockIdx.x * region : skeys;
+    double* vals = global ? gvals + (long long)blockIdx.x * region : svals;
+    for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) {
+      keys[k] = EMPTY32;
+      vals[k] = 0.0;
+    }
+    __syncthreads();
+    const int* cp = a.col + s;
+    const float* wp = wf + s;
+    for (int e0 = wid * 32; e0 < d; e0 += blockDim.x) {   // warp-uniform 32-entry chunks
+      int j;
+      float w;
+      load_entry_f(a, cp, wp, d, e0 + lane, pol, j, w);
+      const int lbl = entry_label<ASYNC>(a, nullptr, e0 + lane, j, v, pol);
+      const unsigned m = __match_any_sync(FULL, lbl);
+      double sum = 0.0;
+      for (int k = 0; k < 32; ++k) {
+        const double x = (double)__shfl_sync(FULL, w, k);
+        if ((m >> k) & 1u) sum += x;
+      }
+      if (lbl >= 0 && (m & lanemask_lt()) == 0) {
+        if (global) fslot_add<true>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
+        else fslot_add<false>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
+      }
+    }
+    if (global) __threadfence_block();
+    __syncthreads();
+    double bs = -1.0;
+    int bl = -1;
+    for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) {
+      const unsigned key = global ? __ldcg(keys + k) : keys[k];
+      if (key == EMPTY32) continue;
+      const double val = global ? __ldcg(vals + k) : vals[k];
+      if (fbetter(val, (int)key, bs, bl)) {
+        bs = val;
+        bl = (int)key;
+      }
+    }
+    fbest_reduce<32>(bs, bl);
+    if (lane == 0) {
+      s_bs[wid] = bs;
+      s_bl[wid] = bl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+        if (fbetter(s_bs[k], s_bl[k], bs, bl)) {
+          bs = s_bs[k];
+          bl = s_bl[k];
+        }
+      const int old = own_label<ASYNC>(a, v);
+      const int nl = bl >= 0 ? bl : old;
+      const bool changed = nl != old;
+      store_label<ASYNC>(a, v, nl, changed);
+      if (changed) count_graph_change(a, v);
+      my_scan += (unsigned long long)d;
+      my_dn += changed ? 1ull : 0ull;
+      s_changed = changed;
+    }
+    __syncthreads();
+    if (s_changed && a.mark) {
+      for (int e = threadIdx.x; e < d; e += blockDim.x) {
+        const int jj = ld_stream(cp + e, pol.stream);
+        if ((unsigned)jj < (unsigned)a.n) a.fnext[jj] = 1;
+      }
+      if (!ASYNC && threadIdx.x == 0) a.fnext[v] = 1;
+    }
+    __syncthreads();
+  }
+  flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// ------------------------------------------------------------- Eq. 1, f64
+// Per vertex K_i (float64 sum of its row), S1 += weights of its entries in
+// its own community, Sigma[C_i] += K_i; then S2 = sum Sigma_c^2.
+__global__ void __launch_bounds__(256) mod_f_rows_kernel(const long long* __restrict__ off, const int* __restrict__ col,
+                                                         const float* __restrict__ wf, const int* __restrict__ labels,
+                                                         long long n, double* __restrict__ sigma, double* sums,
+                                                         Counters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  double tk = 0.0, ts1 = 0.0;
+  for (long long u = warp; u < n; u += nwarps) {
+    const int cu = labels[u];
+    if ((unsigned)cu >= (unsigned)n) {
+      if (lane == 0) raise_err(&ctr->err, ERRBIT_INVALID);
+      continue;
+    }
+    double k = 0.0;
+    for (long long x = off[u] + lane; x < off[u + 1]; x += 32) {
+      const int j = col[x];
+      const float w = wf[x];
+      if ((unsigned)j >= (unsigned)n || !(w > 0.f && w <= FLT_MAX)) {
+        raise_err(&ctr->err, ERRBIT_INVALID);
+        continue;
+      }
+      k += (double)w;
+      if (labels[j] == cu) ts1 += (double)w;
+    }
+    for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
+    if (lane == 0 && k != 0.0) atomicAdd(sigma + cu, k);
+    tk += lane == 0 ? k : 0.0;
+  }
+  for (int o = 16; o; o >>= 1) {
+    tk += __shfl_xor_sync(FULL, tk, o);
+    ts1 += __shfl_xor_sync(FULL, ts1, o);
+  }
+  if (lane == 0) {
+    if (tk != 0.0) atomicAdd(sums, tk);
+    if (ts1 != 0.0) atomicAdd(sums + 1, ts1);
+  }
+}
+
+__global__ void __launch_bounds__(256) mod_f_square_kernel(const double* __restrict__ sigma, long long n, double* sums) {
+  double acc = 0.0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    acc += sigma[c] * sigma[c];
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(sums + 2, acc);
+}
+
+// ---------------------------------------------------------------- launchers
+namespace {
+template <bool A>
+cudaError_t launch_f_t(const SweepArgs& a, const float* wf, int cls, unsigned* gkeys, double* gvals,
+                       long long region, const DeviceInfo& di, cudaStream_t s) {
+  const int grid = 8 * di.sm_count;
+  switch (cls) {
+    case 0: sweep_f_group_kernel<1, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
+    case 1: sweep_f_group_kernel<2, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
+    case 2: sweep_f_group_kernel<4, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
+    case 3: sweep_f_group_kernel<8, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
+    case 4: sweep_f_group_kernel<16, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
+    case 5: sweep_f_group_kernel<32, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
+    default: {
+      const unsigned tb = F_TABLE_SLOTS;
+      const size_t smem = (size_t)tb * (sizeof(double) + sizeof(unsigned));
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(sweep_f_block_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+      }
+      sweep_f_block_kernel<A><<<F_BLOCKS_PER_SM * di.sm_count, F_BLOCK, smem, s>>>(a, wf, cls, tb, gkeys, gvals,
+                                                                                   region);
+    }
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+}  // namespace
+
+long long float_table_blocks(const DeviceInfo& di) { return (long long)F_BLOCKS_PER_SM * di.sm_count; }
+
+cudaError_t launch_sweep_f32(const SweepArgs& a, const float* wf, int cls, bool async_mode, unsigned* gkeys,
+                             double* gvals, long long region, const DeviceInfo& di, cudaStream_t s) {
+  return async_mode ? launch_f_t<true>(a, wf, cls, gkeys, gvals, region, di, s)
+                    : launch_f_t<false>(a, wf, cls, gkeys, gvals, region, di, s);
+}
+
+cudaError_t launch_modularity_f32(const long long* off, const int* col, const float* wf, const int* labels,
+                                  long long n, double* sigma, double* sums, Counters* ctr, const DeviceInfo& di,
+                                  cudaStream_t s) {
+  cudaMemsetAsync(sigma, 0, sizeof(double) * (size_t)n, s);
+  cudaMemsetAsync(sums, 0, sizeof(double) * 3, s);
+  mod_f_rows_kernel<<<16 * di.sm_count, 256, 0, s>>>(off, col, wf, labels, n, sigma, sums, ctr);
+  mod_f_square_kernel<<<8 * di.sm_count, 256, 0, s>>>(sigma, n, sums);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace gsl

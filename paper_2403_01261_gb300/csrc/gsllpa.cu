@@ -39,6 +39,11 @@ struct gsl_ctx {
 
   unsigned* rowbits = nullptr;          // row-start bitmap of the streaming identity sweep
   long long cap_rowbits = 0;
+  unsigned* fkeys = nullptr;            // float-weight sweep: global table regions (keys, sums)
+  double* fvals = nullptr;
+  long long cap_fkeys = 0, cap_fvals = 0;
+  int* work2 = nullptr;                 // worklist of the rows the majority filter leaves
+  long long cap_work2 = 0;
   int* lg = nullptr;                    // labels gathered per CSR entry (two-phase sweeps)
   long long cap_lg = 0;
   unsigned long long* wtab = nullptr;   // warp-kernel fallback tables
@@ -201,12 +206,15 @@ int map_err(gsl_ctx* c, int bits, const char* where) {
 }
 
 // ------------------------------------------------------------- profiling
-enum Slot { SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + NCLASS, SL_COUNT, SL_MOD, SL_IDENT, SL_PRE, SL_N };
+enum Slot {
+  SL_CLASSIFY = 0, SL_INIT, SL_BIN, SL_SWEEP0, SL_SPLIT = SL_SWEEP0 + NCLASS, SL_COUNT, SL_MOD, SL_IDENT, SL_PRE,
+  SL_FILTER, SL_N
+};
 const char* slot_name(int k) {
   static const char* names[SL_N] = {"classify", "init_labels", "bin_frontier", "sweep_deg1", "sweep_deg2",
                                     "sweep_deg3_4", "sweep_deg5_8", "sweep_deg9_16", "sweep_deg17_32",
                                     "sweep_warp_small", "sweep_warp_large", "sweep_block", "sweep_hub",
-                                    "split_unionfind", "split_count_renumber", "modularity", "sweep1_stream", "pregather"};
+                                    "split_unionfind", "split_count_renumber", "modularity", "sweep1_stream", "pregather", "majority_filter"};
   return names[k];
 }
 
@@ -389,13 +397,24 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     // one that changed more than half of the vertices is run on all
     // vertices: marking would select nearly everything anyway.
     a.mark = (t > 1 && 2 * dn_prev <= n) ? 1 : 0;
-    // once fewer than half of the vertices changed, most rows keep a
-    // majority of their own label: test that before building a table
-    a.majority = (!a.ident && !a.check &&
-                  (c->tune.majority == 2 || (c->tune.majority == 1 && t > 1 && 2 * dn_prev < n))) ? 1 : 0;
+    // from sweep 3 on, most long rows keep a majority of their own label
+    // (sweep 2 reads the labels of sweep 1, which are nearly all distinct):
+    // filter those out before the tables
+    const bool filter = !a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
+    SweepArgs af = a;   // classes 7 and 8 after the filter read its worklist
+    if (filter) {
+      if (int r = grow(c, c->work2, c->cap_work2, n)) return r;
+      const int pe = prof_begin(c, s);
+      CK(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, s));
+      prof_end(c, pe, SL_FILTER, s, 2);
+      af.work = c->work2;
+    }
     for (int k = 0; k < NCLASS; ++k) {
       const int pe = prof_begin(c, s);
-      if (k == CLS_HUB && c->hub_ready) {
+      if (k == CLS_WARP_L || k == CLS_BLOCK) {
+        CK(launch_sweep_class(af, k, weights != nullptr, async_mode, c->tune, c->di, s));
+        prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+      } else if (k == CLS_HUB && c->hub_ready) {
         HubPlan hp{c->hub_piece_start, c->hub_ustart, c->hub_best, c->hub_own,
                    c->hub_wsum,        c->hub_used_cnt, c->hub_used, c->hub_tab};
         c->hub_dirty = true;   // until this sweep is known to have finished cleanly
@@ -426,6 +445,21 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
         sl.bytes += per_v * (double)v + per_e * (double)e;
         act_all += v;
       }
+      if (filter) {
+        // the filter read every row of classes 7 and 8: the settled ones (their
+        // entries are in `scanned` but in no class) and those it passed on
+        long long cls_e = 0, rows = (long long)c->ctr_h->fast_active;
+        for (int k = 0; k < NCLASS; ++k) cls_e += (long long)c->ctr_h->cls_scanned[k];
+        long long fe = (long long)c->ctr_h->scanned - cls_e;
+        for (int k = CLS_WARP_L; k <= CLS_BLOCK; ++k) {
+          fe += (long long)c->ctr_h->cls_scanned[k];
+          rows += c->ctr_h->cls_count[k];
+        }
+        auto& sf = c->profile.slot[SL_FILTER];
+        sf.vertices += rows;
+        sf.entries += fe;
+        sf.bytes += per_v * (double)rows + per_e * (double)fe;
+      }
       auto& sb = c->profile.slot[SL_BIN];
       sb.vertices += all_active ? n : act_all;
       sb.bytes += (all_active ? 0.0 : (double)n) + (all_active ? 16.0 * (double)n : 16.0 * (double)act_all) +
@@ -435,6 +469,80 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     c->hub_dirty = false;   // every hub's final pass reset the slots its pieces claimed
     const long long dn = (long long)c->ctr_h->dn;
     long long act = (long long)c->ctr_h->fast_active;
+    for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
+    scanned += (long long)c->ctr_h->scanned;
+    if (st && t <= GSL_STATS_SWEEPS) {
+      st->changed[t - 1] = dn;
+      st->active[t - 1] = act;
+    }
+    marked_prev = a.mark != 0;
+    dn_prev = dn;
+    if ((double)dn / (double)n <= tol) {
+      converged = true;
+      break;
+    }
+  }
+  if (st) {
+    st->iterations = t;
+    st->converged = converged ? 1 : 0;
+    st->edges_scanned = scanned;
+  }
+  *final = async_mode ? c->lab[0] : c->lab[t & 1];
+  return GSL_OK;
+}
+
+// The sweep loop with float32 weights and float64 sums (float_kernels.cu):
+// the same frontier, stop test and statistics as run_lpa, without the
+// integer-only devices (streaming first sweep, two-phase gathers, majority
+// filter, hub pieces).
+int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* labels_init, double tol,
+                int32_t max_iters, int32_t mode, gsl_stats* st, cudaStream_t s, int** final) {
+  const long long n = g->n;
+  const bool async_mode = mode == GSL_MODE_ASYNC;
+  const long long maxd = c->ctr_h->max_degree;
+  const long long region = 2 * (maxd > 0 ? maxd : 1);
+  if (2 * maxd > 8192) {   // rows whose table does not fit shared memory
+    const long long need = float_table_blocks(c->di) * region;
+    if (int r = grow(c, c->fkeys, c->cap_fkeys, need)) return r;
+    if (int r = grow(c, c->fvals, c->cap_fvals, need)) return r;
+  }
+  CK(cudaMemsetAsync(c->flag[0], 0, (size_t)n, s));
+  CK(cudaMemsetAsync(c->flag[1], 0, (size_t)n, s));
+  CK(launch_init_labels(labels_init, c->lab[0], async_mode ? nullptr : c->lab[1], n, c->ctr, c->di, s));
+  SweepArgs a{};
+  a.off = OFF(g);
+  a.col = g->cols;
+  a.ctr = c->ctr;
+  a.work = c->work;
+  a.n = n;
+  int t = 0;
+  bool converged = false, marked_prev = false;
+  long long dn_prev = n, scanned = 0;
+  while (t < max_iters) {
+    ++t;
+    if (int r = reset_sweep_counters(c, s)) return r;
+    const bool all_active = t == 1 || !marked_prev;
+    {
+      const int pe = prof_begin(c, s);
+      CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s));
+      prof_end(c, pe, SL_BIN, s, 1);
+    }
+    a.prev = async_mode ? c->lab[0] : c->lab[(t - 1) & 1];
+    a.next = async_mode ? c->lab[0] : c->lab[t & 1];
+    a.fnext = c->flag[(t + 1) & 1];
+    a.check = t == 1 ? 1 : 0;
+    a.mark = (t > 1 && 2 * dn_prev <= n) ? 1 : 0;
+    for (int k = 0; k < NCLASS; ++k) {
+      const int pe = prof_begin(c, s);
+      CK(launch_sweep_f32(a, wf, k, async_mode, c->fkeys, c->fvals, region, c->di, s));
+      prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+    }
+    CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->prof) prof_resolve(c);
+    if (int r = map_err(c, c->ctr_h->err, "lpa_f32")) return r;
+    const long long dn = (long long)c->ctr_h->dn;
+    long long act = 0;
     for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
     scanned += (long long)c->ctr_h->scanned;
     if (st && t <= GSL_STATS_SWEEPS) {
@@ -597,11 +705,19 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
     a.ident = (!async_mode && t == 1) ? 1 : 0;
     a.check = t == 1 ? 1 : 0;
     a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
-    a.majority = (!a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3))) ? 1 : 0;
+    const bool filter = !a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
     a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
+    SweepArgs af = a;
+    if (filter) {
+      pe = prof ? prof_begin(c, cs) : -1;
+      ck(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, cs));
+      if (prof) prof_end(c, pe, SL_FILTER, cs, 2);
+      af.work = c->work2;
+    }
     for (int k = 0; k < NCLASS; ++k) {
       pe = prof ? prof_begin(c, cs) : -1;
-      ck(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, cs));
+      ck(launch_sweep_class(k == CLS_WARP_L || k == CLS_BLOCK ? af : a, k, weights != nullptr, async_mode, c->tune,
+                            c->di, cs));
       if (prof) prof_end(c, pe, SL_SWEEP0 + k, cs, 1);
     }
     ck(launch_graph_update(t, tol, max_iters, c->vptr, num_graphs, c->dn_graph, c->iters, c->done, c->stop, cs));
@@ -665,7 +781,7 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   if (!c) return GSL_OK;
   DeviceGuard dg(c->device);
   void* dptrs[] = {c->lab[0], c->lab[1], c->flag[0], c->flag[1], c->work, c->parent, c->rank, c->sigma,
-                   c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->hub_piece_start,
+                   c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->work2, c->fkeys, c->fvals, c->hub_piece_start,
                    c->hub_ustart, c->hub_best, c->hub_own, c->hub_wsum, c->hub_used_cnt, c->hub_used, c->hub_tab,
                    c->ctr, c->sums, c->k_dev,
                    c->st_off, c->st_col, c->st_w, c->st_lab};
@@ -863,6 +979,83 @@ int gsl_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
   return GSL_OK;
 }
 
+int gsl_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* weights, const int32_t* labels_init, double tol,
+                int32_t max_iters, int32_t mode, int32_t* labels_out, gsl_stats* st, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_lpa_args(c, g, tol, max_iters, mode, labels_out)) return r;
+  if (g->nnz > 0 && !weights) return fail(c, GSL_ERR_INVALID, "weights is NULL");
+  if (st) memset(st, 0, sizeof(*st));
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  CK(cudaEventRecord(c->ev[0], s));
+  if (int r = prepare_graph(c, g, s)) return r;
+  int* fin = nullptr;
+  if (int r = run_lpa_f32(c, g, weights, labels_init, tol, max_iters, mode, st, s, &fin)) return r;
+  CK(cudaMemcpyAsync(labels_out, fin, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaEventRecord(c->ev[1], s));
+  CK(cudaEventSynchronize(c->ev[1]));
+  if (st) cudaEventElapsedTime(&st->ms_lpa, c->ev[0], c->ev[1]);
+  return GSL_OK;
+}
+
+int gsl_gsllpa_f32(gsl_ctx* c, const gsl_csr* g, const float* weights, double tol, int32_t max_iters, int32_t mode,
+                   int32_t* labels_out, gsl_stats* st, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_lpa_args(c, g, tol, max_iters, mode, labels_out)) return r;
+  if (g->nnz > 0 && !weights) return fail(c, GSL_ERR_INVALID, "weights is NULL");
+  if (st) memset(st, 0, sizeof(*st));
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  CK(cudaEventRecord(c->ev[0], s));
+  if (int r = prepare_graph(c, g, s)) return r;
+  int* fin = nullptr;
+  if (int r = run_lpa_f32(c, g, weights, nullptr, tol, max_iters, mode, st, s, &fin)) return r;
+  CK(cudaEventRecord(c->ev[1], s));
+  long long k = 0;
+  if (int r = run_split(c, g, fin, labels_out, 0, &k, s)) return r;
+  CK(cudaEventRecord(c->ev[2], s));
+  CK(cudaEventSynchronize(c->ev[2]));
+  if (st) {
+    cudaEventElapsedTime(&st->ms_lpa, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&st->ms_split, c->ev[1], c->ev[2]);
+    st->communities = k;
+  }
+  return GSL_OK;
+}
+
+int gsl_modularity_f32(gsl_ctx* c, const gsl_csr* g, const float* weights, const int32_t* labels, double* q_out,
+                       void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (int r = check_csr(c, g)) return r;
+  if (!q_out) return fail(c, GSL_ERR_INVALID, "q_out is NULL");
+  if (g->n > 0 && !labels) return fail(c, GSL_ERR_INVALID, "labels is NULL");
+  if (g->nnz > 0 && !weights) return fail(c, GSL_ERR_INVALID, "weights is NULL");
+  *q_out = 0.0;
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  if (int r = prepare_graph(c, g, s)) return r;
+  if (int r = grow(c, c->sigma, c->cap_sigma, g->n)) return r;   // n doubles (8 bytes, as the u64 sums)
+  double* sums = reinterpret_cast<double*>(c->sums);
+  CK(launch_modularity_f32(OFF(g), g->cols, weights, labels, g->n, reinterpret_cast<double*>(c->sigma), sums, c->ctr,
+                           c->di, s));
+  double h[3];
+  CK(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (int r = map_err(c, c->ctr_h->err, "modularity_f32")) return r;
+  *q_out = h[0] == 0.0 ? 0.0 : h[1] / h[0] - h[2] / (h[0] * h[0]);
+  return GSL_OK;
+}
+
 int gsl_split(gsl_ctx* c, const gsl_csr* g, const int32_t* labels_in, int32_t* labels_out, int32_t renumber,
               int64_t* k_out, void* stream) {
   if (!c) return GSL_ERR_INVALID;
@@ -1008,6 +1201,7 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
   if (int r = ensure_vertex_scratch(c, n > 0 ? n : 1)) return r;
   if (int r = grow(c, c->gid, c->cap_gid, n)) return r;
   if (int r = grow(c, c->lab_tmp, c->cap_lab_tmp, n)) return r;
+  if (int r = grow(c, c->work2, c->cap_work2, n > 0 ? n : 1)) return r;
   if (int r = grow(c, c->vptr, c->cap_vptr, (long long)num_graphs + 1)) return r;
   if (int r = grow(c, c->dn_graph, c->cap_dng, num_graphs)) return r;
   if (int r = grow(c, c->iters, c->cap_iters, num_graphs)) return r;
@@ -1027,7 +1221,8 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
   const std::vector<long long> key = {(long long)OFF(g), (long long)g->cols, (long long)weights, n, g->nnz,
                                       num_graphs, max_iters, mode, (long long)(tol * 1e12), c->ctr_h->max_degree,
                                       (long long)c->lab[0], (long long)c->wtab, (long long)c->btab,
-                                      c->tune.warp_max, c->tune.blk_max};
+                                      c->tune.warp_max, c->tune.blk_max, (long long)c->work2,
+                                      c->tune.majority, c->tune.blk_block, c->tune.blk_slots};
   long long graph_launches = 0;
   if (n > 0) {
     if (c->batch_direct) {

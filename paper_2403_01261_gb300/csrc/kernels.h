@@ -30,7 +30,6 @@ struct SweepArgs {
   int ident;                 // prev is the identity labelling (not read)
   int check;                 // validate weights and weighted degrees
   int mark;                  // mark neighbours of changed vertices in fnext
-  int majority;              // test for an own-label majority before building a table
   const int* lg;             // sync mode: labels gathered per entry, lg[e] = prev[col[e]] (null: gather)
 };
 
@@ -70,6 +69,12 @@ cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool 
                                const DeviceInfo& di, cudaStream_t s);
 void count_launches(long long k);   // process-wide tally of kernels this library launched
 long long launches_total();
+// Own-label majority filter over classes 7 and 8: settled rows keep their
+// label; the others go to `out` (n ints, class regions as in the worklist)
+// and become the class counts of the table kernels, which must then read
+// `out` as their worklist.
+cudaError_t launch_majority_filter(const SweepArgs& a, int* out, bool weighted, bool async_mode,
+                                   const DeviceInfo& di, cudaStream_t s);
 // Edge-parallel label gather for a synchronous sweep: lg[e] = prev[col[e]]
 // for every CSR entry (-1 for an out-of-range column).
 cudaError_t launch_pregather(const int* col, long long nnz, const int* prev, long long n, int* lg,
@@ -114,6 +119,18 @@ struct HubPlan {
 bool hub_pieces_fit(const Tuning& t);
 cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weighted, bool async_mode, const Tuning& t,
                               const DeviceInfo& di, cudaStream_t s);
+
+// float_kernels.cu: sweeps with float32 weights and float64 sums.  Classes
+// 6..9 use one block per row; rows whose 2 d slots exceed shared memory use
+// the block's region (`region` slots, >= 2 * largest degree) of gkeys/gvals,
+// float_table_blocks(di) regions in all.
+long long float_table_blocks(const DeviceInfo& di);
+cudaError_t launch_sweep_f32(const SweepArgs& a, const float* wf, int cls, bool async_mode, unsigned* gkeys,
+                             double* gvals, long long region, const DeviceInfo& di, cudaStream_t s);
+// Eq. 1 with float weights: sums[0] = 2m, sums[1] = S1, sums[2] = S2 (sigma: n doubles).
+cudaError_t launch_modularity_f32(const long long* off, const int* col, const float* wf, const int* labels,
+                                  long long n, double* sigma, double* sums, Counters* ctr, const DeviceInfo& di,
+                                  cudaStream_t s);
 
 // split_kernels.cu
 cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels,

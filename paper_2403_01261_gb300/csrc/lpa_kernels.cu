@@ -363,19 +363,6 @@ __global__ void __launch_bounds__(256, 3) sweep_warp_kernel(SweepArgs a, int cls
     unsigned long long best = 0, wsum = 0;
     bool done = false;
     if (a.ident && !ASYNC) done = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, pol, best, wsum));
-    if (!done && a.majority) {   // an own-label majority settles the row without a table
-      unsigned ow = 0, tw = 0;
-      own_weight_pass<WEIGHTED, ASYNC>(a, v, old, cp, wp, a.lg ? a.lg + s : nullptr, d, lane, 32, pol, ow, tw);
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        ow += __shfl_xor_sync(FULL, ow, o);
-        tw += __shfl_xor_sync(FULL, tw, o);
-      }
-      if (2ull * ow > (unsigned long long)tw) {
-        done = true;
-        best = 0;   // nl = old below
-      }
-    }
     if (!done) {
       best = 0;
       wsum = 0;
@@ -477,32 +464,7 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
         __syncthreads();
       }
     }
-    bool settled = false;
-    if (!sorted && a.majority) {
-      // every row of the launch takes this pass and its barrier, so the
-      // per-warp slots of row parity `par` are no longer read by any thread
-      // when the row after next writes them
-      unsigned ow = 0, tw = 0;
-      own_weight_pass<WEIGHTED, ASYNC>(a, v, old, cp, wp, lp, d, threadIdx.x, blockDim.x, pol, ow, tw);
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        ow += __shfl_xor_sync(FULL, ow, o);
-        tw += __shfl_xor_sync(FULL, tw, o);
-      }
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      if (lane == 0) {
-        sh.maj[par][0][wid] = ow;
-        sh.maj[par][1][wid] = tw;
-      }
-      __syncthreads();
-      unsigned long long o_all = 0, t_all = 0;
-      for (int k = 0; k < nw; ++k) {
-        o_all += sh.maj[par][0][k];
-        t_all += sh.maj[par][1][k];
-      }
-      settled = 2 * o_all > t_all;
-    }
-    if (!sorted && !settled) {
+    if (!sorted) {
       const unsigned want = 2u * (unsigned)d;
       int ovf = 1;
       if (!(gthresh > 0 && d > gthresh)) {
@@ -513,8 +475,8 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
       }
       if (ovf) block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
     }
-    unsigned long long b = settled ? 0ull : sh.best[par];
-    const unsigned own_sum = settled ? 0u : sh.own[par];
+    unsigned long long b = sh.best[par];
+    const unsigned own_sum = sh.own[par];
     if (own_sum) {
       const unsigned long long k = pack_key(own_sum, old);
       b = k > b ? k : b;
@@ -522,7 +484,7 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
     const int nl = b ? (int)~(unsigned)b : old;
     const bool changed = nl != old;
     if (threadIdx.x == 0) {
-      if (WEIGHTED && a.check && !settled && sh.wsum[par] >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+      if (WEIGHTED && a.check && sh.wsum[par] >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
       store_label<ASYNC>(a, v, nl, changed);
       if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;
@@ -542,6 +504,80 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
     v1 = v2;
   }
   flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// ---------------------------------------------------------------------------
+// Own-label majority filter for classes 7 and 8 (rows of 257..blk_max
+// entries by default: long enough that one extra lean pass costs less than
+// a table), run before their table kernels once labels have started to
+// settle.  One warp per row, no shared memory (so full occupancy and many
+// rows in flight): the weight of the row's entries carrying the vertex's
+// own label is compared with the row's total (the vertex itself excluded).
+// A strict majority is Eq. 2's argmax: the label stays and the row is done.
+// Other rows are appended to `out` at their class's region and counted in
+// Counters::uns_count; filter_counts_kernel then makes those the class
+// counts for the table kernels.
+template <bool WEIGHTED, bool ASYNC>
+__global__ void __launch_bounds__(256) majority_filter_kernel(SweepArgs a, int* __restrict__ out) {
+  if (stopped(a)) return;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const Pol pol = make_pol();
+  const long long c7 = a.ctr->cls_count[CLS_WARP_L];
+  const long long total = c7 + a.ctr->cls_count[CLS_BLOCK];
+  unsigned long long my_scan = 0, my_settled = 0;
+  for (long long i = warp; i < total; i += nwarps) {
+    const int cls = i < c7 ? CLS_WARP_L : CLS_BLOCK;
+    const long long start = a.ctr->cls_start[cls];
+    const int v = a.work[start + (i < c7 ? i : i - c7)];
+    const long long s = a.off[v];
+    const int d = (int)(a.off[v + 1] - s);
+    const int old = own_label<ASYNC>(a, v);
+    unsigned ow = 0, tw = 0;
+    own_weight_pass<WEIGHTED, ASYNC>(a, v, old, a.col + s, a.w + s, a.lg ? a.lg + s : nullptr, d, lane, 32, pol, ow,
+                                     tw);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      ow += __shfl_xor_sync(FULL, ow, o);
+      tw += __shfl_xor_sync(FULL, tw, o);
+    }
+    if (lane == 0) {
+      if (2ull * ow > (unsigned long long)tw) {
+        store_label<ASYNC>(a, v, old, false);
+        my_scan += (unsigned long long)d;
+        my_settled += 1;
+      } else {
+        out[start + atomicAdd(&a.ctr->uns_count[cls], 1u)] = v;
+      }
+    }
+  }
+  my_scan = warp_sum_u64(my_scan);
+  my_settled = warp_sum_u64(my_settled);
+  if (lane == 0) {
+    if (my_scan) atomicAdd(&a.ctr->scanned, my_scan);
+    if (my_settled) atomicAdd(&a.ctr->fast_active, my_settled);
+  }
+}
+
+__global__ void filter_counts_kernel(Counters* ctr, const int* stop) {
+  if (stop && *(volatile const int*)stop) return;
+  for (int k = CLS_WARP_L; k <= CLS_BLOCK; ++k) ctr->cls_count[k] = ctr->uns_count[k];
+}
+
+cudaError_t launch_majority_filter(const SweepArgs& a, int* out, bool weighted, bool async_mode,
+                                   const DeviceInfo& di, cudaStream_t s) {
+  const int grid = 16 * di.sm_count;
+  if (weighted) {
+    if (async_mode) majority_filter_kernel<true, true><<<grid, 256, 0, s>>>(a, out);
+    else majority_filter_kernel<true, false><<<grid, 256, 0, s>>>(a, out);
+  } else {
+    if (async_mode) majority_filter_kernel<false, true><<<grid, 256, 0, s>>>(a, out);
+    else majority_filter_kernel<false, false><<<grid, 256, 0, s>>>(a, out);
+  }
+  filter_counts_kernel<<<1, 1, 0, s>>>(a.ctr, a.stop);
+  count_launches(2);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -148,7 +148,6 @@ struct BlockRowShared {
   unsigned long long best[2], wsum[2];
   unsigned used[2], own[2];
   int ovf[2];
-  unsigned maj[2][2][32];   // per warp: (own-label weight, total weight) of the majority pass
 };
 
 // Own-label majority pass: one lean pass over the row sums, per thread, the

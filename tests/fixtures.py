@@ -26,3 +26,16 @@ def load_disconnected40():
                 rec[key] = int(vals[0])
     g = I.from_edges(rec["n"], rec["edges"], name="disconnected40")
     return g, rec
+
+
+def float_weights(g, seed, dyadic=True):
+    """Symmetric float32 weights: multiples of 1/8 in [0.125, 4] (sums exact
+    in float64 in any order) or arbitrary values in (0.01, 3)."""
+    rng = np.random.default_rng(seed)
+    src = np.repeat(np.arange(g.n), np.diff(g.offsets))
+    lo = np.minimum(src, g.cols).astype(np.int64)
+    hi = np.maximum(src, g.cols).astype(np.int64)
+    key = lo * g.n + hi
+    uniq, inv = np.unique(key, return_inverse=True)
+    vals = (rng.integers(1, 33, uniq.shape[0]) / 8.0) if dyadic else rng.uniform(0.01, 3.0, uniq.shape[0])
+    return vals[inv].astype(np.float32)

@@ -14,6 +14,7 @@ from scipy.sparse.csgraph import connected_components
 
 import inputs as I
 import oracle as O
+from fixtures import float_weights
 
 
 # ------------------------------------------------------------------ helpers
@@ -416,3 +417,78 @@ def test_sampled_sweep_equals_full_sweep_on_the_sample():
         assert np.array_equal(O.sync_sweep_at(h, prev, sel), full[sel])
     with pytest.raises(ValueError):
         O.sync_sweep_at(h, prev, [g.n])
+
+
+# --------------------------------------- float32 weights with float64 sums
+def dense_float_sweep(g, wf, prev):
+    n = g.n
+    A = np.zeros((n, n), dtype=np.float64)
+    src = np.repeat(np.arange(n), np.diff(g.offsets))
+    np.add.at(A, (src, g.cols), wf.astype(np.float64))
+    np.fill_diagonal(A, 0.0)
+    Y = np.zeros((n, n), dtype=np.float64)
+    Y[np.arange(n), prev] = 1.0
+    S = A @ Y
+    has = A.sum(axis=1) > 0
+    return np.where(has, np.argmax(S, axis=1), prev).astype(np.int32), S
+
+
+def test_float_sweep_matches_dense_product():
+    rng = np.random.default_rng(41)
+    for trial in range(60):
+        n = int(rng.integers(2, 30))
+        g = I.random_graph(n, float(rng.uniform(0.1, 0.6)), seed=500 + trial)
+        if g.nnz == 0:
+            continue
+        prev = rng.integers(0, max(1, n // 3), n).astype(np.int32)
+        wf = float_weights(g, trial, dyadic=True)   # exact sums: the argmax is exact too
+        got, dn = O.sync_sweep_f32(g, wf, prev)
+        want, _ = dense_float_sweep(g, wf, prev)
+        assert np.array_equal(got, want) and dn == int((got != prev).sum())
+        wf = float_weights(g, trial, dyadic=False)  # rounding may differ: compare clear winners only
+        got, _ = O.sync_sweep_f32(g, wf, prev)
+        want, S = dense_float_sweep(g, wf, prev)
+        top2 = -np.sort(-S, axis=1)[:, :2] if n > 1 else np.zeros((n, 2))
+        clear = (top2[:, 0] - top2[:, 1]) > 1e-9 * np.maximum(1.0, top2[:, 0])
+        assert np.array_equal(got[clear], want[clear])
+
+
+def test_float_lpa_with_integer_weights_equals_integer_lpa():
+    for seed in range(4):
+        g = I.rmat(9, 8, seed=seed)
+        wi = I.symmetric_weights(g, seed, 6)
+        h = I.Graph(g.offsets, g.cols, wi)
+        lab_i, t_i, dn_i = O.lpa_sync(h, 0.05, 20)
+        lab_f, t_f, dn_f = O.lpa_sync_f32(g, wi.astype(np.float32), 0.05, 20)
+        assert t_i == t_f and np.array_equal(lab_i, lab_f) and np.array_equal(dn_i, dn_f)
+        assert O.modularity_f64(g, wi.astype(np.float32), lab_i) == pytest.approx(O.modularity(h, lab_i), abs=1e-12)
+
+
+def test_float_modularity_matches_networkx():
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(43)
+    for trial in range(30):
+        n = int(rng.integers(2, 40))
+        g = I.random_graph(n, float(rng.uniform(0.05, 0.4)), seed=700 + trial)
+        if g.nnz == 0:
+            continue
+        wf = float_weights(g, trial, dyadic=False)
+        labels = rng.integers(0, max(1, n // 4), n).astype(np.int32)
+        G = nx.Graph()
+        G.add_nodes_from(range(n))
+        src = np.repeat(np.arange(n), np.diff(g.offsets))
+        for a, b, w in zip(src, g.cols, wf):
+            if a < b:
+                G.add_edge(int(a), int(b), weight=float(w))
+        comms = [set(np.nonzero(labels == c)[0].tolist()) for c in np.unique(labels)]
+        assert O.modularity_f64(g, wf, labels) == pytest.approx(nx.community.modularity(G, comms, weight="weight"),
+                                                                abs=1e-12)
+
+
+def test_float_weights_must_be_finite_and_positive():
+    g = I.path(4)
+    for bad in (0.0, -1.0, np.nan, np.inf):
+        wf = np.ones(g.nnz, dtype=np.float32)
+        wf[1] = bad
+        with pytest.raises(ValueError):
+            O.sync_sweep_f32(g, wf, np.arange(4, dtype=np.int32))
