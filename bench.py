@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--scale", type=int, default=25, help="R-MAT scale of the workload")
     p.add_argument("--edge-factor", type=int, default=24)
     p.add_argument("--mode", choices=["sync", "async"], default="sync")
+    p.add_argument("--weights", choices=["unit", "int", "f32"], default="unit",
+                   help="edge weights: unit (the benchmark), int32 1..32 or float32 k/8 for k in 1..32, "
+                        "both from a hash of the endpoint pair (symmetric)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-scale", type=int, default=19, help="R-MAT scale of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -111,6 +114,23 @@ def workload_graph(scale, edge_factor, cache, rank, world):
     offsets = np.load(off_p, mmap_mode="r")
     cols = np.load(col_p, mmap_mode="r")
     return offsets, cols
+
+
+def edge_weights(off, col, kind):
+    """Symmetric synthetic weights on the device: a hash of the unordered
+    endpoint pair picks k in 1..32; int32 k or float32 k/8 (exact in float64
+    sums)."""
+    import torch
+    n = off.numel() - 1
+    rows = torch.repeat_interleave(torch.arange(n, device=off.device, dtype=torch.int64), off[1:] - off[:-1])
+    a = torch.minimum(rows, col.to(torch.int64))
+    b = torch.maximum(rows, col.to(torch.int64))
+    del rows
+    h = (a * 0x9E3779B1 + b * 0x85EBCA6B) & 0xFFFFFFFF
+    h = (h ^ (h >> 15)) * 0x2C1B3C6D & 0xFFFFFFFF
+    k = ((h >> 11) & 31) + 1
+    del a, b, h
+    return k.to(torch.int32) if kind == "int" else (k.to(torch.float32) / 8.0)
 
 
 # -------------------------------------------------------------------- clocks
@@ -577,13 +597,20 @@ def main():
     ctx = gsl.Context(local)
     mode = 1 if args.mode == "async" else 0
     stream = torch.cuda.current_stream(dev)
+    wt = edge_weights(off, col, args.weights) if args.weights != "unit" else None
+    if args.weights == "f32":
+        def step(**kw):
+            return ctx.gsllpa_f32(off, col, wt, tolerance=0.05, max_iters=20, mode=mode, out=out, **kw)
+    else:
+        def step(**kw):
+            return ctx.gsllpa(off, col, wt, tolerance=0.05, max_iters=20, mode=mode, out=out, **kw)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
     for _ in range(args.warmup):
-        ctx.gsllpa(off, col, tolerance=0.05, max_iters=20, mode=mode, out=out)
+        step()
     torch.cuda.synchronize(dev)
 
     # timed region: K steps on resident inputs (cols >> L2, so no flush needed)
@@ -596,7 +623,7 @@ def main():
         torch.cuda.synchronize(dev)
         ev0.record(stream)
         for _ in range(args.steps):
-            _, st = ctx.gsllpa(off, col, tolerance=0.05, max_iters=20, mode=mode, out=out, stats=True)
+            _, st = step(stats=True)
             stats.append(st)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
@@ -609,7 +636,7 @@ def main():
 
     # end to end through the host-buffer entry point (copies inside the region)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.weights == "unit":
         lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
         ctx.gsllpa_host(off_h, col_h, tolerance=0.05, max_iters=20, mode=mode, out=lab_h)   # warm the staging
         barrier()
@@ -649,9 +676,10 @@ def main():
     line = {
         "metric": METRIC, "value": replicas_value(world, nnz, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32", "data": "synthetic",
+        "dtype": "f32 weights, f64 sums" if args.weights == "f32" else "int32", "data": "synthetic",
         "config": {"workload": f"rmat{args.scale}-ef{args.edge_factor}", "rmat_abcd": [0.57, 0.19, 0.19, 0.05],
                    "n": n, "nnz": nnz, "tolerance": 0.05, "max_iters": 20, "mode": args.mode, "seed": 1,
+                   "weights": args.weights,
                    "parallelism": f"replicas{world}", "l2": f"inputs larger than L2 (cols {4 * nnz / 1e9:.2f} GB)"},
         "sweeps": T, "communities": st["communities"], "lpa_ms": lpa_ms, "split_ms": split_ms,
         "edges_iter_per_s": world * nnz * T / (ms * 1e-3),

@@ -322,10 +322,12 @@ int gsl_ctx_set_batch_mode(gsl_ctx* ctx, int32_t use_cuda_graph);
  * each with its own context, CUDA stream and device buffers that stay
  * resident for the server's life.  A free worker admits the oldest waiting
  * requests that fit its buffers (admission by device memory), packs them
- * into one batch CSR on the device and runs gsl_gsllpa_batch on it; requests
- * that arrive while batches are running are admitted by the next worker to
- * free up, so the work of different requests overlaps on the GPU.  Every
- * request gets exactly its solo gsl_gsllpa result.
+ * into one batch CSR on the device and runs gsl_gsllpa_batch on it; a
+ * request of 2^22 entries or more keeps the GPU busy on its own and is run
+ * alone through gsl_gsllpa.  Requests that arrive while batches are running
+ * are admitted by the next worker to free up, so the work of different
+ * requests overlaps on the GPU.  Every request gets exactly its solo
+ * gsl_gsllpa result.
  * --------------------------------------------------------------------- */
 typedef struct gsl_server gsl_server;
 

@@ -83,6 +83,11 @@ struct gsl_server {
 
 namespace {
 
+// A request of at least this many CSR entries keeps the GPU busy on its own
+// and runs alone through the single-graph path (streaming first sweep, hub
+// pieces, majority filter); smaller ones are packed into batches.
+constexpr int64_t SOLO_ENTRIES = 1ll << 22;
+
 void worker_loop(gsl_server* S, int w) {
   Slot& sl = S->slots[w];
   int dev = S->cfg.device;
@@ -97,11 +102,14 @@ void worker_loop(gsl_server* S, int w) {
       int64_t v = 0, e = 0;
       while (!S->queue.empty() && (int)batch.size() < maxg) {
         Request* r = S->queue.front();
+        const bool solo = r->nnz >= SOLO_ENTRIES;
+        if (solo && !batch.empty()) break;                              // a large request goes alone
         if (v + r->n > S->cap_v || e + r->nnz > S->cap_e) break;   // FIFO: the head waits for a free slot
         S->queue.pop_front();
         v += r->n;
         e += r->nnz;
         batch.push_back(r);
+        if (solo) break;
       }
     }
     if (batch.empty()) continue;
@@ -119,6 +127,42 @@ void worker_loop(gsl_server* S, int w) {
     }
     int rc = GSL_OK;
     cudaStream_t s = sl.stream;
+    if (G == 1 && batch[0]->nnz >= SOLO_ENTRIES) {
+      Request* r = batch[0];
+      gsl_stats st{};
+      if (cudaMemcpyAsync(sl.off, r->offsets, sizeof(int64_t) * (size_t)(r->n + 1), cudaMemcpyHostToDevice, s) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(sl.col, r->cols, sizeof(int32_t) * (size_t)r->nnz, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = GSL_ERR_CUDA;
+      gsl_csr csr{r->n, r->nnz, reinterpret_cast<const int64_t*>(sl.off), sl.col};
+      if (rc == GSL_OK)
+        rc = gsl_gsllpa(sl.ctx, &csr, nullptr, S->cfg.tolerance, S->cfg.max_iters, S->cfg.mode, sl.lab, &st, s);
+      if (rc == GSL_OK &&
+          (cudaMemcpyAsync(sl.lab_h, sl.lab, sizeof(int32_t) * (size_t)r->n, cudaMemcpyDeviceToHost, s) !=
+               cudaSuccess ||
+           cudaStreamSynchronize(s) != cudaSuccess))
+        rc = GSL_ERR_CUDA;
+      if (rc != GSL_OK) cudaGetLastError();
+      const auto t_done = clk::now();
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->status = rc;
+        if (rc == GSL_OK) {
+          r->labels.assign(sl.lab_h, sl.lab_h + r->n);
+          r->sweeps = st.iterations;
+        }
+        r->t_start = t_start;
+        r->t_done = t_done;
+        r->batch_graphs = 1;
+        r->done = true;
+      }
+      S->cv_done.notify_all();
+      S->batches++;
+      S->graphs_in_batches += 1;
+      S->completed += 1;
+      S->busy_workers--;
+      continue;
+    }
     // pack: copy every solo CSR to its place, then shift offsets and columns
     for (int k = 0; k < G && rc == GSL_OK; ++k) {
       Request* r = batch[k];

@@ -77,3 +77,23 @@ def test_server_async_mode_invariants(gpu_lib):
         assert (lab <= v).all() and np.array_equal(lab[lab], lab)
         assert O.disconnected(g, lab)[0] == 0
     srv.close()
+
+
+def test_server_large_requests_run_alone(gpu_lib):
+    """A request of 2^22 entries or more runs alone through the single-graph
+    path, between batched small ones; every result is its solo result."""
+    big = I.rmat(17, 24, seed=8)
+    assert big.nnz >= 1 << 22
+    small = [I.batched_sbm(k, n_lo=500, n_hi=3000) for k in range(6)]
+    gs = [small[0], big, small[1], small[2], big, small[3], small[4], small[5]]
+    want = [O.gsl_lpa(g, 0.05, 20)[0] for g in gs]
+    srv = gpu_lib.Server(slots=2, slot_vertices=400_000, slot_entries=8_000_000, max_batch_graphs=8)
+    ids = [srv.submit(g.offsets, g.cols) for g in gs]
+    infos = []
+    for k, rid in enumerate(ids):
+        lab, info = srv.wait(rid, info=True)
+        assert np.array_equal(lab, want[k]), gs[k].name
+        infos.append(info)
+    assert all(infos[k]["batch_graphs"] == 1 for k in (1, 4))
+    assert infos[1]["sweeps"] == O.lpa_sync(big, 0.05, 20)[1]
+    srv.close()

@@ -30,6 +30,13 @@ MUTANTS = {
     "seq_no_reactivation": ("for (int64_t e = off[i]; e < off[i + 1]; ++e) processed[col[e]] = 0;", ""),
     "alg4_off_by_one": ("if (reached < S[c])", "if (reached <= S[c])"),
     "lp_split_no_community_test": ("if (C[j] == C[i] && Cp[j] < cmin) cmin = Cp[j];", "if (Cp[j] < cmin) cmin = Cp[j];"),
+    "float_tie_to_largest_label": (
+        "(W[c] == bestw && c < best)) { best = c; bestw = W[c]; }\n  }\n  for (int64_t k = 0; k < nt; ++k) W[touched[k]] = 0.0;",
+        "(W[c] == bestw && c > best)) { best = c; bestw = W[c]; }\n  }\n  for (int64_t k = 0; k < nt; ++k) W[touched[k]] = 0.0;"),
+    "float_weights_ignored": ("W[c] += (double)w[e];", "W[c] += 1.0;"),
+    "float_sigma_indexed_by_vertex": ("Sigma[C[i]] += K;\n  }\n  double s2 = 0.0;", "Sigma[i] += K;\n  }\n  double s2 = 0.0;"),
+    "float_self_loop_counted": ("    if (j == i) continue;\n    int32_t c = C[j];\n    if (W[c] == 0.0)",
+                                "    int32_t c = C[j];\n    if (W[c] == 0.0)"),
 }
 
 PINS = [
@@ -52,6 +59,10 @@ PINS = [
     (P.test_modularity_path_split_by_hand, {}),
     (P.test_modularity_matches_networkx_and_pair_sum, {}),
     (P.test_disconnected_checker_by_hand_and_vs_scipy, {}),
+    (P.test_float_sweep_matches_dense_product, {}),
+    (P.test_float_self_loop_is_ignored_by_hand, {}),
+    (P.test_float_lpa_with_integer_weights_equals_integer_lpa, {}),
+    (P.test_float_modularity_matches_networkx, {}),
 ]
 
 

@@ -453,6 +453,17 @@ def test_float_sweep_matches_dense_product():
         assert np.array_equal(got[clear], want[clear])
 
 
+def test_float_self_loop_is_ignored_by_hand():
+    # vertex 0: self-loop of weight 10 plus edge to 1 (weight 0.5); vertex 2 isolated
+    A = np.zeros((3, 3), dtype=np.int64)
+    A[0, 0] = 10
+    A[0, 1] = A[1, 0] = 1
+    g = graph_from_adj(A)
+    wf = np.where(g.cols == np.repeat(np.arange(3), np.diff(g.offsets)), 10.0, 0.5).astype(np.float32)
+    nxt, dn = O.sync_sweep_f32(g, wf, np.array([0, 1, 2], dtype=np.int32))
+    assert nxt.tolist() == [1, 0, 2] and dn == 2
+
+
 def test_float_lpa_with_integer_weights_equals_integer_lpa():
     for seed in range(4):
         g = I.rmat(9, 8, seed=seed)
