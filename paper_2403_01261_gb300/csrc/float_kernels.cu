@@ -63,6 +63,25 @@ __device__ __forceinline__ void load_entry_f(const SweepArgs& a, const int* cp, 
   }
 }
 
+// Sum of w over the lanes of mask m in ascending lane order (row order),
+// for every lane at once: the loop runs as often as the largest mask has
+// bits, one shuffle per step.
+__device__ __forceinline__ double group_sum(unsigned m, float w) {
+  const int lane = threadIdx.x & 31;
+  const int steps = __reduce_max_sync(FULL, (unsigned)__popc(m));
+  double sum = 0.0;
+  unsigned mm = m;
+  for (int t = 0; t < steps; ++t) {
+    const int src = mm ? __ffs(mm) - 1 : lane;
+    const double x = (double)__shfl_sync(FULL, w, src);
+    if (mm) {
+      sum += x;
+      mm &= mm - 1;
+    }
+  }
+  return sum;
+}
+
 // Adds c to label lbl's sum in an open-addressing table of cap slots.
 template <bool GLOBAL>
 __device__ __forceinline__ void fslot_add(unsigned* keys, double* vals, unsigned cap, unsigned lbl, double c,
@@ -110,12 +129,7 @@ __global__ void __launch_bounds__(256) sweep_f_group_kernel(SweepArgs a, const f
     load_entry_f(a, a.col + s, wf + s, d, gl, pol, j, w);
     const int lbl = entry_label<ASYNC>(a, nullptr, gl, j, v, pol);
     const unsigned m = __match_any_sync(FULL, lbl) & gmask;
-    double sum = 0.0;   // this lane's label, its group's weights in lane order
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-      const double x = (double)__shfl_sync(FULL, w, gbase + k);
-      if ((m >> (gbase + k)) & 1u) sum += x;
-    }
+    const double sum = group_sum(m, w);   // this lane's label: its group's weights in lane order
     double bs = sum;
     int bl = lbl;
     fbest_reduce<G>(bs, bl);
@@ -152,6 +166,7 @@ __global__ void __launch_bounds__(F_BLOCK) sweep_f_block_kernel(SweepArgs a, con
   __shared__ double s_bs[F_BLOCK / 32];
   __shared__ int s_bl[F_BLOCK / 32];
   __shared__ int s_changed;
+  __shared__ double s_own;
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
   const Pol pol = make_pol();
@@ -169,25 +184,31 @@ __global__ void __launch_bounds__(F_BLOCK) sweep_f_block_kernel(SweepArgs a, con
       keys[k] = EMPTY32;
       vals[k] = 0.0;
     }
+    if (threadIdx.x == 0) s_own = 0.0;
+    const int old = own_label<ASYNC>(a, v);
     __syncthreads();
     const int* cp = a.col + s;
     const float* wp = wf + s;
+    double own_acc = 0.0;   // entries carrying the vertex's own label stay out of the table
     for (int e0 = wid * 32; e0 < d; e0 += blockDim.x) {   // warp-uniform 32-entry chunks
       int j;
       float w;
       load_entry_f(a, cp, wp, d, e0 + lane, pol, j, w);
-      const int lbl = entry_label<ASYNC>(a, nullptr, e0 + lane, j, v, pol);
-      const unsigned m = __match_any_sync(FULL, lbl);
-      double sum = 0.0;
-      for (int k = 0; k < 32; ++k) {
-        const double x = (double)__shfl_sync(FULL, w, k);
-        if ((m >> k) & 1u) sum += x;
+      int lbl = entry_label<ASYNC>(a, nullptr, e0 + lane, j, v, pol);
+      if (lbl == old) {
+        own_acc += (double)w;
+        lbl = -1;
       }
+      if (__ballot_sync(FULL, lbl >= 0) == 0) continue;
+      const unsigned m = __match_any_sync(FULL, lbl);
+      const double sum = group_sum(m, w);
       if (lbl >= 0 && (m & lanemask_lt()) == 0) {
         if (global) fslot_add<true>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
         else fslot_add<false>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
       }
     }
+    for (int o = 16; o; o >>= 1) own_acc += __shfl_xor_sync(FULL, own_acc, o);
+    if (lane == 0 && own_acc != 0.0) atomicAdd(&s_own, own_acc);
     if (global) __threadfence_block();
     __syncthreads();
     double bs = -1.0;
@@ -213,7 +234,10 @@ __global__ void __launch_bounds__(F_BLOCK) sweep_f_block_kernel(SweepArgs a, con
           bs = s_bs[k];
           bl = s_bl[k];
         }
-      const int old = own_label<ASYNC>(a, v);
+      if (s_own > 0.0 && fbetter(s_own, old, bs, bl)) {
+        bs = s_own;
+        bl = old;
+      }
       const int nl = bl >= 0 ? bl : old;
       const bool changed = nl != old;
       store_label<ASYNC>(a, v, nl, changed);
@@ -233,6 +257,64 @@ __global__ void __launch_bounds__(F_BLOCK) sweep_f_block_kernel(SweepArgs a, con
     __syncthreads();
   }
   flush_counters(a.ctr, cls, my_dn, my_scan);
+}
+
+// ------------------------------------------------------- sweep 1, streamed
+// From the identity labels a strictly increasing row holds every label once
+// (its neighbour's id) with that entry's weight, so Eq. 2 picks the
+// neighbour of largest weight, the smallest id among equal weights.  One
+// warp per row of the rows the check pass left unflagged.
+__global__ void __launch_bounds__(256) ident_max_f_kernel(const long long* __restrict__ off, long long n,
+                                                          const int* __restrict__ col, const float* __restrict__ wf,
+                                                          const unsigned char* __restrict__ bad,
+                                                          int* __restrict__ next, Counters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_dn = 0, my_scan = 0, my_act = 0;
+  for (long long v = warp; v < n; v += nwarps) {
+    const long long st = off[v];
+    const int d = (int)(off[v + 1] - st);
+    if (d == 0 || bad[v]) continue;   // warp-uniform
+    double bw = -1.0;
+    int bj = -1;
+    for (int x = lane; x < d; x += 32) {
+      const int j = col[st + x];
+      const float w = wf[st + x];
+      if (!(w > 0.f && w <= FLT_MAX)) raise_err(&ctr->err, ERRBIT_INVALID);
+      if (j == (int)v || (unsigned)j >= (unsigned)n) continue;
+      if (fbetter((double)w, j, bw, bj)) {
+        bw = (double)w;
+        bj = j;
+      }
+    }
+    fbest_reduce<32>(bw, bj);
+    if (lane == 0) {
+      const int nl = bj >= 0 ? bj : (int)v;
+      next[v] = nl;
+      my_dn += nl != (int)v ? 1ull : 0ull;
+      my_scan += (unsigned long long)d;
+      my_act += 1;
+    }
+  }
+  my_dn = warp_sum_u64(my_dn);
+  my_scan = warp_sum_u64(my_scan);
+  my_act = warp_sum_u64(my_act);
+  if (lane == 0) {
+    if (my_dn) atomicAdd(&ctr->dn, my_dn);
+    if (my_scan) atomicAdd(&ctr->scanned, my_scan);
+    if (my_act) atomicAdd(&ctr->fast_active, my_act);
+  }
+}
+
+cudaError_t launch_ident_stream_f32(const long long* off, long long n, const int* col, const float* wf,
+                                    long long nnz, unsigned* bits, unsigned char* bad, int* next, Counters* ctr,
+                                    const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (cudaError_t e = launch_row_check(off, n, col, nnz, bits, bad, ctr, di, s)) return e;
+  ident_max_f_kernel<<<16 * di.sm_count, 256, 0, s>>>(off, n, col, wf, bad, next, ctr);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- Eq. 1, f64

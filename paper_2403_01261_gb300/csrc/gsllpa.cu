@@ -521,7 +521,17 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
   while (t < max_iters) {
     ++t;
     if (int r = reset_sweep_counters(c, s)) return r;
-    const bool all_active = t == 1 || !marked_prev;
+    bool all_active = t == 1 || !marked_prev;
+    if (t == 1 && !async_mode && !labels_init) {
+      // sweep 1 from the identity labels streams the strictly increasing
+      // rows; the others (flagged in flag[1]) go through the table kernels
+      if (int r = grow(c, c->rowbits, c->cap_rowbits, (g->nnz >> 5) + 1)) return r;
+      const int pe = prof_begin(c, s);
+      CK(launch_ident_stream_f32(OFF(g), n, g->cols, wf, g->nnz, c->rowbits, c->flag[1], c->lab[1], c->ctr, c->di,
+                                 s));
+      prof_end(c, pe, SL_IDENT, s, 3);
+      all_active = false;
+    }
     {
       const int pe = prof_begin(c, s);
       CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s));
@@ -542,7 +552,7 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
     if (c->prof) prof_resolve(c);
     if (int r = map_err(c, c->ctr_h->err, "lpa_f32")) return r;
     const long long dn = (long long)c->ctr_h->dn;
-    long long act = 0;
+    long long act = (long long)c->ctr_h->fast_active;
     for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
     scanned += (long long)c->ctr_h->scanned;
     if (st && t <= GSL_STATS_SWEEPS) {

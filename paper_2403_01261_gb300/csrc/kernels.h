@@ -84,6 +84,14 @@ cudaError_t launch_pregather(const int* col, long long nnz, const int* prev, lon
 // `bad` (n bytes, zero on entry) and left for the hash kernels.
 cudaError_t launch_ident_stream(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
                                 unsigned char* bad, int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+// The first two of those passes (row starts, strict-increase check).
+cudaError_t launch_row_check(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
+                             unsigned char* bad, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+// Streaming sweep 1 with float weights: for strictly increasing rows the
+// label is the neighbour of largest weight (smallest id among equals).
+cudaError_t launch_ident_stream_f32(const long long* off, long long n, const int* col, const float* wf,
+                                    long long nnz, unsigned* bits, unsigned char* bad, int* next, Counters* ctr,
+                                    const DeviceInfo& di, cudaStream_t s);
 cudaError_t launch_init_labels(const int* init, int* a, int* b, long long n, Counters* ctr,
                                const DeviceInfo& di, cudaStream_t s);
 long long block_grid_size(const Tuning& t, const DeviceInfo& di);   // blocks of the class 8/9 kernel

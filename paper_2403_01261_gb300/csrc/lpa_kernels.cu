@@ -729,15 +729,23 @@ __global__ void ident_first_kernel(const long long* __restrict__ off, long long 
   }
 }
 
-cudaError_t launch_ident_stream(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
-                                unsigned char* bad, int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+cudaError_t launch_row_check(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
+                             unsigned char* bad, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int g = 8 * di.sm_count;
   cudaMemsetAsync(bits, 0, sizeof(unsigned) * (size_t)((nnz >> 5) + 1), s);
   rowstart_kernel<<<g, 256, 0, s>>>(off, n, bits);
   if (nnz > 0) sorted_check_kernel<<<g, 256, 0, s>>>(off, n, col, nnz, bits, bad, ctr);
-  ident_first_kernel<<<g, 256, 0, s>>>(off, n, col, bad, next, ctr);
-  count_launches(nnz > 0 ? 3 : 2);
+  count_launches(nnz > 0 ? 2 : 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ident_stream(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
+                                unsigned char* bad, int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (cudaError_t e = launch_row_check(off, n, col, nnz, bits, bad, ctr, di, s)) return e;
+  ident_first_kernel<<<8 * di.sm_count, 256, 0, s>>>(off, n, col, bad, next, ctr);
+  count_launches(1);
   return cudaGetLastError();
 }
 
