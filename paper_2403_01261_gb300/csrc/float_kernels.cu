@@ -21,7 +21,6 @@ namespace gsl {
 
 namespace {
 
-constexpr unsigned EMPTY32 = 0xFFFFFFFFu;
 constexpr int F_BLOCK = 256;            // threads per block of the table kernel
 constexpr unsigned F_TABLE_SLOTS = 8192;  // shared-memory slots per block (12 bytes each)
 constexpr int F_BLOCKS_PER_SM = 2;
@@ -262,8 +261,22 @@ __global__ void __launch_bounds__(F_BLOCK) sweep_f_block_kernel(SweepArgs a, con
 // ------------------------------------------------------- sweep 1, streamed
 // From the identity labels a strictly increasing row holds every label once
 // (its neighbour's id) with that entry's weight, so Eq. 2 picks the
-// neighbour of largest weight, the smallest id among equal weights.  One
-// warp per row of the rows the check pass left unflagged.
+// neighbour of largest weight, the smallest id among equal weights.  Rows
+// the check pass flagged are left for the table kernels.
+__device__ __forceinline__ void f_stream_entry(const int* col, const float* wf, long long e, long long v, long long n,
+                                               Counters* ctr, double& bw, int& bj) {
+  const int j = col[e];
+  const float w = wf[e];
+  if (!(w > 0.f && w <= FLT_MAX)) raise_err(&ctr->err, ERRBIT_INVALID);
+  if (j == (int)v || (unsigned)j >= (unsigned)n) return;
+  if (fbetter((double)w, j, bw, bj)) {
+    bw = (double)w;
+    bj = j;
+  }
+}
+
+// A warp takes 32 consecutive vertices: each lane scans its own row when it
+// has at most 32 entries, then the warp scans the longer rows together.
 __global__ void __launch_bounds__(256) ident_max_f_kernel(const long long* __restrict__ off, long long n,
                                                           const int* __restrict__ col, const float* __restrict__ wf,
                                                           const unsigned char* __restrict__ bad,
@@ -272,29 +285,44 @@ __global__ void __launch_bounds__(256) ident_max_f_kernel(const long long* __res
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   unsigned long long my_dn = 0, my_scan = 0, my_act = 0;
-  for (long long v = warp; v < n; v += nwarps) {
-    const long long st = off[v];
-    const int d = (int)(off[v + 1] - st);
-    if (d == 0 || bad[v]) continue;   // warp-uniform
-    double bw = -1.0;
-    int bj = -1;
-    for (int x = lane; x < d; x += 32) {
-      const int j = col[st + x];
-      const float w = wf[st + x];
-      if (!(w > 0.f && w <= FLT_MAX)) raise_err(&ctr->err, ERRBIT_INVALID);
-      if (j == (int)v || (unsigned)j >= (unsigned)n) continue;
-      if (fbetter((double)w, j, bw, bj)) {
-        bw = (double)w;
-        bj = j;
-      }
+  for (long long base = warp * 32; base < n; base += nwarps * 32) {   // warp-uniform
+    const long long v = base + lane;
+    long long st = 0;
+    int d = 0;
+    bool mine = false;
+    if (v < n) {
+      st = off[v];
+      d = (int)(off[v + 1] - st);
+      mine = d > 0 && !bad[v];
     }
-    fbest_reduce<32>(bw, bj);
-    if (lane == 0) {
+    if (mine && d <= 32) {
+      double bw = -1.0;
+      int bj = -1;
+      for (int x = 0; x < d; ++x) f_stream_entry(col, wf, st + x, v, n, ctr, bw, bj);
       const int nl = bj >= 0 ? bj : (int)v;
       next[v] = nl;
       my_dn += nl != (int)v ? 1ull : 0ull;
       my_scan += (unsigned long long)d;
       my_act += 1;
+    }
+    unsigned longm = __ballot_sync(FULL, mine && d > 32);
+    while (longm) {
+      const int src = __ffs(longm) - 1;
+      longm &= longm - 1;
+      const long long vv = __shfl_sync(FULL, v, src);
+      const long long sst = __shfl_sync(FULL, st, src);
+      const int dd = __shfl_sync(FULL, d, src);
+      double bw = -1.0;
+      int bj = -1;
+      for (int x = lane; x < dd; x += 32) f_stream_entry(col, wf, sst + x, vv, n, ctr, bw, bj);
+      fbest_reduce<32>(bw, bj);
+      if (lane == src) {
+        const int nl = bj >= 0 ? bj : (int)vv;
+        next[vv] = nl;
+        my_dn += nl != (int)vv ? 1ull : 0ull;
+        my_scan += (unsigned long long)dd;
+        my_act += 1;
+      }
     }
   }
   my_dn = warp_sum_u64(my_dn);
@@ -315,6 +343,88 @@ cudaError_t launch_ident_stream_f32(const long long* off, long long n, const int
   ident_max_f_kernel<<<16 * di.sm_count, 256, 0, s>>>(off, n, col, wf, bad, next, ctr);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// Class 6 (33..256 entries): one warp per row with its own shared table of
+// F_WARP_SLOTS (label, float64 sum) slots; own-label entries are summed
+// outside the table; the warp scans its table for the argmax.
+constexpr int F_WARP_SLOTS = 512;   // 2 * 256
+constexpr int F_WARP_BLOCK = 128;   // 4 warps, 4 * 512 * 12 bytes = 24 KB
+
+template <bool ASYNC>
+__global__ void __launch_bounds__(F_WARP_BLOCK) sweep_f_warp_kernel(SweepArgs a, const float* __restrict__ wf,
+                                                                   int cls) {
+  __shared__ double svals_all[(F_WARP_BLOCK / 32) * F_WARP_SLOTS];
+  __shared__ unsigned skeys_all[(F_WARP_BLOCK / 32) * F_WARP_SLOTS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* vals = svals_all + wid * F_WARP_SLOTS;
+  unsigned* keys = skeys_all + wid * F_WARP_SLOTS;
+  const unsigned cnt = a.ctr->cls_count[cls];
+  const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
+  const Pol pol = make_pol();
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_dn = 0, my_scan = 0;
+  for (long long item = warp; item < (long long)cnt; item += nwarps) {
+    const int v = work[item];
+    const long long s = a.off[v];
+    const int d = (int)(a.off[v + 1] - s);
+    const unsigned cap = 2u * (unsigned)d;   // <= F_WARP_SLOTS for this class
+    for (unsigned k = lane; k < cap; k += 32) {
+      keys[k] = EMPTY32;
+      vals[k] = 0.0;
+    }
+    __syncwarp();
+    const int old = own_label<ASYNC>(a, v);
+    double own_acc = 0.0;
+    for (int e0 = 0; e0 < d; e0 += 32) {
+      int j;
+      float w;
+      load_entry_f(a, a.col + s, wf + s, d, e0 + lane, pol, j, w);
+      int lbl = entry_label<ASYNC>(a, nullptr, e0 + lane, j, v, pol);
+      if (lbl == old) {
+        own_acc += (double)w;
+        lbl = -1;
+      }
+      if (__ballot_sync(FULL, lbl >= 0) == 0) continue;
+      const unsigned m = __match_any_sync(FULL, lbl);
+      const double sum = group_sum(m, w);
+      if (lbl >= 0 && (m & lanemask_lt()) == 0) fslot_add<false>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
+    }
+    __syncwarp();
+    double bs = -1.0;
+    int bl = -1;
+    for (unsigned k = lane; k < cap; k += 32) {
+      const unsigned key = keys[k];
+      if (key != EMPTY32 && fbetter(vals[k], (int)key, bs, bl)) {
+        bs = vals[k];
+        bl = (int)key;
+      }
+    }
+    for (int o = 16; o; o >>= 1) own_acc += __shfl_xor_sync(FULL, own_acc, o);
+    if (own_acc > 0.0 && fbetter(own_acc, old, bs, bl)) {   // the same on every lane
+      bs = own_acc;
+      bl = old;
+    }
+    fbest_reduce<32>(bs, bl);
+    const int nl = bl >= 0 ? bl : old;
+    const bool changed = nl != old;
+    if (lane == 0) {
+      store_label<ASYNC>(a, v, nl, changed);
+      if (changed) count_graph_change(a, v);
+      my_scan += (unsigned long long)d;
+      my_dn += changed ? 1ull : 0ull;
+    }
+    if (changed && a.mark) {
+      for (int x = lane; x < d; x += 32) {
+        const int jj = ld_stream(a.col + s + x, pol.stream);
+        if ((unsigned)jj < (unsigned)a.n) a.fnext[jj] = 1;
+      }
+      if (!ASYNC && lane == 0) a.fnext[v] = 1;
+    }
+    __syncwarp();
+  }
+  flush_counters(a.ctr, cls, my_dn, my_scan);
 }
 
 // ------------------------------------------------------------- Eq. 1, f64
@@ -380,6 +490,9 @@ cudaError_t launch_f_t(const SweepArgs& a, const float* wf, int cls, unsigned* g
     case 3: sweep_f_group_kernel<8, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
     case 4: sweep_f_group_kernel<16, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
     case 5: sweep_f_group_kernel<32, A><<<grid, 256, 0, s>>>(a, wf, cls); break;
+    case 6:   // d <= warp_small <= 256: 2 d slots always fit a warp's table
+      sweep_f_warp_kernel<A><<<4 * grid, F_WARP_BLOCK, 0, s>>>(a, wf, cls);
+      break;
     default: {
       const unsigned tb = F_TABLE_SLOTS;
       const size_t smem = (size_t)tb * (sizeof(double) + sizeof(unsigned));

@@ -136,16 +136,16 @@ __global__ void __launch_bounds__(512, 2) hub_piece_kernel(SweepArgs a, HubPlan 
     const int* lp = a.lg ? a.lg + s + e0 : nullptr;
     const unsigned want = 2u * (unsigned)len;
     const unsigned cap = want < tb ? want : tb;
-    block_row<WEIGHTED, ASYNC, false>(a, v, own, cp, wp, lp, len, smem_h64, cap, 0xFFFFFFFFu, pol, sh, par);
+    const SlotTable st = make_table(smem_h64, tb);
+    block_row<WEIGHTED, ASYNC, false>(a, v, own, cp, wp, lp, len, st, cap, 0xFFFFFFFFu, pol, sh, par);
     // the piece's (label, sum) pairs into the hub's global table
     unsigned long long* tab = hp.tab + 2 * hp.ustart[i];
     const unsigned gcap = (unsigned)(2 * d);
     unsigned long long best = 0;
     for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) {
-      const unsigned long long x = smem_h64[k];
-      if (x == EMPTY64) continue;
-      const unsigned lbl = (unsigned)(x >> 32);
-      const unsigned sum = hub_slot_add(tab, gcap, lbl, (unsigned)x, hp.used + hp.ustart[i], hp.used_cnt + i,
+      const unsigned lbl = st.keys[k];
+      if (lbl == EMPTY32) continue;
+      const unsigned sum = hub_slot_add(tab, gcap, lbl, st.sums[k], hp.used + hp.ustart[i], hp.used_cnt + i,
                                         2 * hp.ustart[i], &a.ctr->err);
       const unsigned long long key = pack_key(sum, (int)lbl);
       best = key > best ? key : best;

@@ -258,7 +258,7 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
                                          const int* lp, int d,
-                                         unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
+                                         SlotTable tab, unsigned cap, unsigned limit, const Pol& pol,
                                          unsigned long long& best, unsigned long long& wsum, unsigned& own_sum) {
   const int lane = threadIdx.x & 31;
   // three rounds in flight: labels of round r+1 and columns of round r+2
@@ -275,7 +275,10 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, 128 + 32 * u + lane, pol, jn[u], wn[u]);
-  for (unsigned k = lane; k < cap; k += 32) tab[k] = EMPTY64;
+  for (unsigned k = lane; k < cap; k += 32) {
+    tab.keys[k] = EMPTY32;
+    tab.sums[k] = 0;
+  }
   __syncwarp();
   unsigned used = 0;
   for (int e0 = 0; e0 < d; e0 += 128) {
@@ -331,10 +334,10 @@ __global__ void __launch_bounds__(256, 3) sweep_warp_kernel(SweepArgs a, int cls
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_w64[];
   const int lane = threadIdx.x & 31;
-  unsigned long long* tab = smem_w64 + (size_t)(threadIdx.x >> 5) * TW;
+  const SlotTable tab = make_table(smem_w64 + (size_t)(threadIdx.x >> 5) * TW, TW);
   const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  unsigned long long* gtab = SPILL ? a.wtab + warp_id * a.wtab_region : nullptr;
+  const SlotTable gtab = SPILL ? make_table(a.wtab + warp_id * a.wtab_region, a.wtab_region) : SlotTable{nullptr, nullptr};
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
   const Pol pol = make_pol();
@@ -421,7 +424,8 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_b64[];
   __shared__ BlockRowShared sh;
-  unsigned long long* gtab = a.btab + (long long)blockIdx.x * a.btab_region;
+  const SlotTable gtab = make_table(a.btab + (long long)blockIdx.x * a.btab_region, a.btab_region);
+  const SlotTable stab = make_table(smem_b64, tb);
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
   const Pol pol = make_pol();
@@ -471,7 +475,7 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
         const unsigned cap = want < tb ? want : tb;
         // each of up to 16 warps may add 32 new slots after the flag is raised
         const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, lp, d, smem_b64, cap, limit, pol, sh, par);
+        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, lp, d, stab, cap, limit, pol, sh, par);
       }
       if (ovf) block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
     }

@@ -110,29 +110,39 @@ __device__ __forceinline__ void store_label(const SweepArgs& a, int v, int nl, b
   else if (changed) __stcg(a.next + v, nl);
 }
 
-// Hash tables of the d > 32 kernels.  A slot is 64 bits, (label << 32 | sum),
-// EMPTY64 when free.  A new label claims a slot with one atomicCAS; an
-// existing label adds its count with one atomicAdd on the whole word (sums
-// stay below 2^31, so the label half never changes).  Linear probing from
+// Hash tables of the d > 32 kernels: two 32-bit arrays, keys (the label,
+// EMPTY32 when free) and sums.  A new label claims a key with atomicCAS;
+// every entry group then adds its count to the sum with a 32-bit atomicAdd,
+// which returns the label's new total (32-bit shared atomics are several
+// times faster than 64-bit ones).  A table of `region` slots lives in
+// `region` 64-bit words: keys first, sums after.  Linear probing from
 // __umulhi(hash, cap), so any capacity works.
+constexpr unsigned EMPTY32 = 0xFFFFFFFFu;
+
+struct SlotTable {
+  unsigned* keys;
+  unsigned* sums;
+};
+
+__device__ __forceinline__ SlotTable make_table(unsigned long long* base, long long region) {
+  unsigned* k = reinterpret_cast<unsigned*>(base);
+  return {k, k + region};
+}
+
 template <bool GLOBAL>
-__device__ __forceinline__ unsigned slot_add(unsigned long long* tab, unsigned cap, unsigned lbl, unsigned c,
-                                             bool& created, int* err) {
+__device__ __forceinline__ unsigned slot_add(SlotTable t, unsigned cap, unsigned lbl, unsigned c, bool& created,
+                                             int* err) {
   unsigned h = __umulhi(hash32(lbl), cap);
-  const unsigned long long mine = ((unsigned long long)lbl << 32) | c;
   for (int p = 0; p < PROBE_CAP; ++p) {
-    unsigned long long x = GLOBAL ? __ldcg(tab + h) : *(volatile unsigned long long*)(tab + h);
-    if (x == EMPTY64) {
-      x = atomicCAS(tab + h, EMPTY64, mine);
-      if (x == EMPTY64) {
+    unsigned k = GLOBAL ? __ldcg(t.keys + h) : *(volatile unsigned*)(t.keys + h);
+    if (k == EMPTY32) {
+      k = atomicCAS(t.keys + h, EMPTY32, lbl);
+      if (k == EMPTY32) {
         created = true;
-        return c;
+        return atomicAdd(t.sums + h, c) + c;
       }
     }
-    if ((unsigned)(x >> 32) == lbl) {
-      const unsigned long long old = atomicAdd(tab + h, (unsigned long long)c);
-      return (unsigned)old + c;
-    }
+    if (k == lbl) return atomicAdd(t.sums + h, c) + c;
     if (++h == cap) h = 0;
   }
   raise_err(err, ERRBIT_TIMEOUT);
@@ -215,7 +225,7 @@ __device__ __forceinline__ void block_publish(const SweepArgs& a, BlockRowShared
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
                                          const int* lp, int d,
-                                         unsigned long long* tab, unsigned cap, unsigned limit, const Pol& pol,
+                                         SlotTable tab, unsigned cap, unsigned limit, const Pol& pol,
                                          BlockRowShared& sh, int par) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int step = nw * 128;
@@ -235,7 +245,10 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, step + cb + u * cu, pol, jn[u], wn[u]);
-  for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) tab[k] = EMPTY64;
+  for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) {
+    tab.keys[k] = EMPTY32;
+    tab.sums[k] = 0;
+  }
   if (threadIdx.x == 0) {
     sh.best[par] = 0;
     sh.wsum[par] = 0;
