@@ -1,5 +1,8 @@
 """Parity at full size, in the launch configuration the benchmark times.
 
+Batched (4096 planted-partition graphs, 3.7 G entries): sampled graphs
+against the oracle and against solo calls.
+
 R-MAT scale 25 (33.5 M vertices, 1.56 G entries): the oracle cannot run
 all sweeps here in reasonable time, so every GPU sweep is checked on
 sampled vertices (random ones, the highest-degree hubs, degree-1 vertices)
@@ -93,3 +96,38 @@ def test_lattice_chains_full_oracle(ctx):
     q_ref = O.modularity(g, want_split)
     assert abs(ctx.modularity(off, col, torch.from_numpy(want_split).to(DEV)) - q_ref) <= REL_Q * max(1.0, abs(q_ref))
     assert ctx.disconnected(off, col, got) == O.disconnected(g, want)[0]
+
+
+def test_batched_4096_graphs_sampled(gpu_lib):
+    """The benchmark's batched workload (4096 planted-partition graphs, one
+    CUDA-graph sweep loop): 24 sampled graphs against the oracle, every 64th
+    graph against its own solo call."""
+    sys.path.insert(0, ROOT)
+    import bench
+    graphs = bench.batched_graphs(4096, 0)
+    G = len(graphs)
+    vptr = np.zeros(G + 1, dtype=np.int64)
+    eptr = np.zeros(G + 1, dtype=np.int64)
+    for k, (o, c) in enumerate(graphs):
+        vptr[k + 1] = vptr[k] + (o.shape[0] - 1)
+        eptr[k + 1] = eptr[k] + c.shape[0]
+    off_u = np.empty(vptr[-1] + 1, dtype=np.int64)
+    col_u = np.empty(eptr[-1], dtype=np.int32)
+    off_u[0] = 0
+    for k, (o, c) in enumerate(graphs):
+        off_u[vptr[k] + 1:vptr[k + 1] + 1] = o[1:] + eptr[k]
+        col_u[eptr[k]:eptr[k + 1]] = c + vptr[k]
+    ctx = gpu_lib.Context(0)
+    labels, iters = ctx.gsllpa_batch(torch.from_numpy(off_u).to(DEV), torch.from_numpy(col_u).to(DEV), vptr)
+    labels = labels.cpu().numpy()
+    rng = np.random.default_rng(4096)
+    for k in sorted(rng.choice(G, 24, replace=False)):
+        o, c = graphs[k]
+        g = I.Graph(o, c)
+        want, t, _ = O.gsl_lpa(g, 0.05, 20)
+        assert iters[k] == t and np.array_equal(labels[vptr[k]:vptr[k + 1]], want), k
+    solo = gpu_lib.Context(0)
+    for k in range(0, G, 64):   # every 64th graph through the plain entry point as well
+        o, c = graphs[k]
+        got = solo.gsllpa(torch.from_numpy(o).to(DEV), torch.from_numpy(c).to(DEV)).cpu().numpy()
+        assert np.array_equal(got, labels[vptr[k]:vptr[k + 1]]), k
