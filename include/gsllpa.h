@@ -124,6 +124,16 @@ int gsl_ctx_set_majority(gsl_ctx* ctx, int32_t mode);
  * statistics do not depend on the mode. */
 int gsl_ctx_set_pregather(gsl_ctx* ctx, int32_t mode);
 
+/* Hub rows (synchronous or asynchronous sweeps, integer weights) whose
+ * degree is at most max_degree are aggregated by one thread-block cluster
+ * of 8 CTAs each: the row's label table is spread over the 8 CTAs' shared
+ * memories and filled with distributed-shared-memory atomics.  A row with
+ * more distinct labels than those tables hold is redone in a global-memory
+ * table.  Longer hubs are cut into pieces of 8192 entries.  0 turns the
+ * clusters off; by default every hub row goes to a cluster.  max_degree
+ * < 0: GSL_ERR_INVALID.  Labels and statistics do not depend on it. */
+int gsl_ctx_set_hub_cluster(gsl_ctx* ctx, int64_t max_degree);
+
 /* Result of gsl_autotune. */
 typedef struct {
   int32_t warp_max;     /* chosen thresholds (now set on the context) */

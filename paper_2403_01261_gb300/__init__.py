@@ -119,6 +119,7 @@ def load():
         lib.gsl_ctx_set_pregather.argtypes = [P, i32]
         lib.gsl_ctx_set_block_config.argtypes = [P, i32, i32]
         lib.gsl_ctx_set_majority.argtypes = [P, i32]
+        lib.gsl_ctx_set_hub_cluster.argtypes = [P, i64]
         lib.gsl_lpa_f32.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_gsllpa_f32.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
         lib.gsl_modularity_f32.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
@@ -229,6 +230,11 @@ class Context:
     def set_majority(self, mode: int):
         """0: never, 1: once labels settle (default), 2: every sweep after the first."""
         self._raise(self._lib.gsl_ctx_set_majority(self._h, int(mode)))
+
+    def set_hub_cluster(self, max_degree: int):
+        """Hubs up to this degree are aggregated by one 8-CTA thread-block
+        cluster each (default: every hub); 0 turns the clusters off."""
+        self._raise(self._lib.gsl_ctx_set_hub_cluster(self._h, int(max_degree)))
 
     def set_pregather(self, mode: int):
         """0: never (default), 1: when the frontier is large, 2: every eligible sweep."""

@@ -35,6 +35,8 @@ struct Counters {
   unsigned long long cls_scanned[NCLASS];  // CSR entries read per class this sweep
   unsigned long long fast_active;          // vertices settled by the streaming identity sweep
   unsigned int hub_pieces;                 // pieces of this sweep's class-9 rows
+  unsigned int hub_clusters;               // class-9 rows taken by thread-block clusters
+  unsigned int hub_clu_next;               // the next of those rows to be taken
   unsigned int pad3;
   unsigned int uns_count[NCLASS];          // majority filter: rows left for the table kernels
   int err;                      // ERRBIT_* (sticky for the call)

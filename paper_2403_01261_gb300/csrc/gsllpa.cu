@@ -57,7 +57,8 @@ struct gsl_ctx {
   unsigned* hub_own = nullptr;
   unsigned long long* hub_wsum = nullptr;
   unsigned* hub_used_cnt = nullptr;
-  long long cap_hub_v = 0;              // entries of each of the six per-hub arrays
+  int* hub_clu = nullptr;
+  long long cap_hub_v = 0;              // entries of each of the seven per-hub arrays
   unsigned* hub_used = nullptr;
   long long cap_hub_used = 0;
   unsigned long long* hub_tab = nullptr;
@@ -283,8 +284,8 @@ int prepare_graph(gsl_ctx* c, const gsl_csr* g, cudaStream_t s) {
   if (c->hub_ready) {
     const long long old_tab = c->cap_hub_tab;
     const unsigned long long* old_ptr = c->hub_tab;
-    if (c->cap_hub_v < hubs + 1) {   // the six per-hub arrays share one capacity
-      long long k0 = 0, k1 = 0, k2 = 0, k3 = 0, k4 = 0, k5 = 0;
+    if (c->cap_hub_v < hubs + 1) {   // the seven per-hub arrays share one capacity
+      long long k0 = 0, k1 = 0, k2 = 0, k3 = 0, k4 = 0, k5 = 0, k6 = 0;
       c->cap_hub_v = 0;
       if (int r = grow(c, c->hub_piece_start, k0, hubs + 1)) return r;
       if (int r = grow(c, c->hub_ustart, k1, hubs + 1)) return r;
@@ -292,6 +293,7 @@ int prepare_graph(gsl_ctx* c, const gsl_csr* g, cudaStream_t s) {
       if (int r = grow(c, c->hub_own, k3, hubs + 1)) return r;
       if (int r = grow(c, c->hub_wsum, k4, hubs + 1)) return r;
       if (int r = grow(c, c->hub_used_cnt, k5, hubs + 1)) return r;
+      if (int r = grow(c, c->hub_clu, k6, hubs + 1)) return r;
       c->cap_hub_v = hubs + 1;
     }
     if (int r = grow(c, c->hub_used, c->cap_hub_used, hub_e)) return r;
@@ -416,10 +418,11 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
         prof_end(c, pe, SL_SWEEP0 + k, s, 1);
       } else if (k == CLS_HUB && c->hub_ready) {
         HubPlan hp{c->hub_piece_start, c->hub_ustart, c->hub_best, c->hub_own,
-                   c->hub_wsum,        c->hub_used_cnt, c->hub_used, c->hub_tab};
+                   c->hub_wsum,        c->hub_used_cnt, c->hub_used, c->hub_tab, c->hub_clu};
         c->hub_dirty = true;   // until this sweep is known to have finished cleanly
-        CK(launch_hub_pieces(a, hp, weights != nullptr, async_mode, c->tune, c->di, s));
-        prof_end(c, pe, SL_SWEEP0 + k, s, 3);
+        int kernels = 0;
+        CK(launch_hub_pieces(a, hp, weights != nullptr, async_mode, filter, c->tune, c->di, s, &kernels));
+        prof_end(c, pe, SL_SWEEP0 + k, s, kernels);
       } else {
         CK(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, s));
         prof_end(c, pe, SL_SWEEP0 + k, s, 1);
@@ -792,7 +795,7 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   DeviceGuard dg(c->device);
   void* dptrs[] = {c->lab[0], c->lab[1], c->flag[0], c->flag[1], c->work, c->parent, c->rank, c->sigma,
                    c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->work2, c->fkeys, c->fvals, c->hub_piece_start,
-                   c->hub_ustart, c->hub_best, c->hub_own, c->hub_wsum, c->hub_used_cnt, c->hub_used, c->hub_tab,
+                   c->hub_ustart, c->hub_best, c->hub_own, c->hub_wsum, c->hub_used_cnt, c->hub_clu, c->hub_used, c->hub_tab,
                    c->ctr, c->sums, c->k_dev,
                    c->st_off, c->st_col, c->st_w, c->st_lab};
   for (void* p : dptrs)
@@ -930,6 +933,13 @@ int gsl_ctx_set_majority(gsl_ctx* c, int32_t mode) {
   if (mode < 0 || mode > 2) return fail(c, GSL_ERR_INVALID, "majority mode must be 0, 1 or 2");
   c->tune.majority = mode;
   c->batch_key.clear();
+  return GSL_OK;
+}
+
+int gsl_ctx_set_hub_cluster(gsl_ctx* c, int64_t max_degree) {
+  if (!c) return GSL_ERR_INVALID;
+  if (max_degree < 0) return fail(c, GSL_ERR_INVALID, "hub cluster degree must be >= 0");
+  c->tune.hub_cluster_max = max_degree > (1ll << 30) ? (1 << 30) : (int)max_degree;
   return GSL_OK;
 }
 

@@ -20,13 +20,20 @@
 //      best key, the label written and counted, the table slots the pieces
 //      claimed are reset (the tables stay empty between sweeps), and the
 //      neighbours of a changed hub are marked.
+#include <cooperative_groups.h>
+
 #include "sweep_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gsl {
 
 namespace {
 
 constexpr int HUB_PIECE = 8192;   // entries per piece (distinct labels <= 8192 < 3/4 of 12288 slots)
+constexpr unsigned HUB_CLUSTER = 8;   // CTAs per cluster of the cluster kernel (the portable maximum)
+constexpr long long HUB_CLU_BIG = 65536;   // cluster rows longer than this are listed first
+constexpr int HUB_DSM_PROBES = 128;        // probe bound of the distributed table (overflow past it)
 
 // Global-table insert that records every slot it claims in `used`.
 __device__ __forceinline__ unsigned hub_slot_add(unsigned long long* tab, unsigned cap, unsigned lbl, unsigned c,
@@ -52,6 +59,29 @@ __device__ __forceinline__ unsigned hub_slot_add(unsigned long long* tab, unsign
   return 0;
 }
 
+// Insert into the cluster's distributed table (see cluster_row): one
+// compare-and-swap per probe claims the slot or finds the label there, and
+// the count is added without waiting for the result (the argmax is read
+// from the tables once every insert has landed).  Returns false when
+// HUB_DSM_PROBES probes found neither: the table is too full.
+__device__ __forceinline__ bool dsm_slot_add(cg::cluster_group& cl, SlotTable t, unsigned cap, unsigned lbl,
+                                             unsigned c) {
+  const unsigned x = hash32(lbl);
+  const unsigned owner = __umulhi(x, HUB_CLUSTER);
+  unsigned* keys = cl.map_shared_rank(t.keys, owner);
+  unsigned* sums = cl.map_shared_rank(t.sums, owner);
+  unsigned h = __umulhi(x * (unsigned)HUB_CLUSTER, cap);
+  for (int p = 0; p < HUB_DSM_PROBES; ++p) {
+    const unsigned k = atomicCAS(keys + h, EMPTY32, lbl);
+    if (k == EMPTY32 || k == lbl) {
+      atomicAdd(sums + h, c);
+      return true;
+    }
+    if (++h == cap) h = 0;
+  }
+  return false;
+}
+
 __device__ __forceinline__ int piece_hub(const int* piece_start, int cnt, int p) {
   int lo = 0, hi = cnt;   // piece_start[lo] <= p < piece_start[hi]
   while (hi - lo > 1) {
@@ -64,14 +94,19 @@ __device__ __forceinline__ int piece_hub(const int* piece_start, int cnt, int p)
 
 }  // namespace
 
-__global__ void __launch_bounds__(1024) hub_plan_kernel(SweepArgs a, HubPlan hp) {
+// Hubs of degree <= cmax go to the cluster kernel (listed in hp.clu) and
+// get no pieces; every hub keeps its global table region and used list.
+__global__ void __launch_bounds__(1024) hub_plan_kernel(SweepArgs a, HubPlan hp, long long cmax) {
   const unsigned cnt = a.ctr->cls_count[CLS_HUB];
   const int* __restrict__ work = a.work + a.ctr->cls_start[CLS_HUB];
   __shared__ long long s_pieces[1024], s_entries[1024];
+  __shared__ int s_clu[1024];
   __shared__ long long base_p, base_e;
+  __shared__ int base_c;
   if (threadIdx.x == 0) {
     base_p = 0;
     base_e = 0;
+    base_c = 0;
   }
   __syncthreads();
   for (unsigned i0 = 0; i0 < cnt; i0 += blockDim.x) {
@@ -85,7 +120,7 @@ __global__ void __launch_bounds__(1024) hub_plan_kernel(SweepArgs a, HubPlan hp)
       hp.wsum[i] = 0;
       hp.used_cnt[i] = 0;
     }
-    s_pieces[threadIdx.x] = (d + HUB_PIECE - 1) / HUB_PIECE;
+    s_pieces[threadIdx.x] = d <= cmax ? 0 : (d + HUB_PIECE - 1) / HUB_PIECE;
     s_entries[threadIdx.x] = d;
     __syncthreads();
     for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scans
@@ -107,11 +142,245 @@ __global__ void __launch_bounds__(1024) hub_plan_kernel(SweepArgs a, HubPlan hp)
     }
     __syncthreads();
   }
+  // the cluster list, rows above HUB_CLU_BIG first (they are taken first,
+  // which shortens the kernel's tail)
+  for (int pass = 0; pass < 2; ++pass) {
+    for (unsigned i0 = 0; i0 < cnt; i0 += blockDim.x) {
+      const unsigned i = i0 + threadIdx.x;
+      bool clu = false;
+      if (i < cnt) {
+        const int v = work[i];
+        const long long d = a.off[v + 1] - a.off[v];
+        clu = d <= cmax && (d > HUB_CLU_BIG) == (pass == 0);
+      }
+      s_clu[threadIdx.x] = clu ? 1 : 0;
+      __syncthreads();
+      for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int xc = threadIdx.x >= (unsigned)o ? s_clu[threadIdx.x - o] : 0;
+        __syncthreads();
+        s_clu[threadIdx.x] += xc;
+        __syncthreads();
+      }
+      if (clu) hp.clu[base_c + s_clu[threadIdx.x] - 1] = (int)i;
+      __syncthreads();
+      if (threadIdx.x == 0) base_c += s_clu[blockDim.x - 1];
+      __syncthreads();
+    }
+  }
   if (threadIdx.x == 0) {
     hp.piece_start[0] = 0;
     hp.ustart[0] = 0;
     a.ctr->hub_pieces = (unsigned)base_p;
+    a.ctr->hub_clusters = (unsigned)base_c;
+    a.ctr->hub_clu_next = 0;
   }
+}
+
+// One CTA's share of hub row v in the cluster kernel.  Virtual thread tid
+// of nthr (all threads of the cluster) takes 32-entry chunks as block_row
+// does, so the whole cluster sweeps the row in rounds of nthr * 4 entries.
+// DSMEM (GLOBAL false): each distinct label of a warp's chunk is added to
+// the cluster's distributed table: the top bits of its hash pick the owning
+// CTA, the rest the first slot of a linear probe in that CTA's table (cap
+// slots).  A probe that finds no slot in HUB_DSM_PROBES steps raises the
+// overflow flag of every CTA in the cluster, and warps stop at their next
+// chunk.  The pass publishes own / wsum in sh[par]; the best key is read
+// from the tables afterwards.  GLOBAL: the row goes to the hub's global
+// table instead (after an overflow), and the best key over the returned
+// totals is published too.  Block-uniform end.
+template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
+__device__ __forceinline__ void cluster_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
+                                            const int* lp, int d, int tid, int nthr, SlotTable tab, unsigned cap,
+                                            unsigned long long* gtab, unsigned gcap, unsigned* gused,
+                                            unsigned* gused_cnt, long long gbase, const Pol& pol,
+                                            BlockRowShared& sh, int par, cg::cluster_group& cl) {
+  const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+  const int step = nw * 128;
+  const int cb = wid * 32 + lane;
+  const int cu = nw * 32;
+  unsigned long long best = 0, wsum = 0;
+  unsigned own_sum = 0;
+  int jn[4], wn[4], ln[4], lw[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, cb + u * cu, pol, jn[u], wn[u]);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
+    ln[u] = entry_label<ASYNC>(a, lp, cb + u * cu, jn[u], v, pol);
+    lw[u] = wn[u];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, step + cb + u * cu, pol, jn[u], wn[u]);
+  if (threadIdx.x == 0) {
+    sh.best[par] = 0;
+    sh.wsum[par] = 0;
+    sh.own[par] = 0;
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < d; r0 += step) {
+    int l[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      l[u] = ln[u];
+      w[u] = lw[u];
+    }
+    if (r0 + step < d) {   // cluster-uniform
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
+        ln[u] = entry_label<ASYNC>(a, lp, r0 + step + cb + u * cu, jn[u], v, pol);
+        lw[u] = wn[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, r0 + 2 * step + cb + u * cu, pol, jn[u], wn[u]);
+    }
+    bool stop = false;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!stop && r0 + (u * nw + wid) * 32 < d) {   // warp-uniform
+        if (!GLOBAL && __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sh.ovf[par] : 0, 0)) {
+          stop = true;
+        } else {
+          const bool mine = l[u] == own;
+          own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
+                              : (unsigned)__popc(__ballot_sync(FULL, mine));
+          if (mine) l[u] = -1;
+          if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
+          const unsigned m = __match_any_sync(FULL, l[u]);
+          const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+          const bool leader = l[u] >= 0 && (m & lanemask_lt()) == 0;
+          if (GLOBAL) {
+            if (leader) {
+              const unsigned sum = hub_slot_add(gtab, gcap, (unsigned)l[u], c, gused, gused_cnt, gbase, &a.ctr->err);
+              const unsigned long long k = pack_key(sum, l[u]);
+              best = k > best ? k : best;
+            }
+          } else {
+            const bool full = leader && !dsm_slot_add(cl, tab, cap, (unsigned)l[u], c);
+            if (__any_sync(FULL, full) && lane == 0) {
+              for (unsigned r = 0; r < HUB_CLUSTER; ++r) *(volatile int*)cl.map_shared_rank(&sh.ovf[par], r) = 1;
+            }
+          }
+        }
+      }
+    }
+    if (stop) break;
+  }
+  block_publish<WEIGHTED>(a, sh, par, best, wsum, own_sum);
+  __syncthreads();
+}
+
+// Hubs of degree <= cmax (listed by the plan kernel), one thread-block
+// cluster at a time: rank 0 takes the next hub from a counter, the row is
+// aggregated in the CTAs' shared tables (cluster_row), each CTA scans its
+// own table for the largest packed key (every label sits in one slot of one
+// table, with its final total) and adds that key, its own-label count and
+// weight to hp.best / hp.own / hp.wsum, which hub_final_kernel reads as it
+// reads the pieces'.  After an overflow
+// (flags read from all CTAs after the second barrier, so the decision is
+// the same in every CTA) the CTAs redo the row in the hub's global table.
+// Two cluster barriers per hub: A after the tables are cleared (no insert
+// can reach a table before it is empty), B after every insert (all flags
+// final).  Per-hub shared values alternate between two copies (par), so a
+// CTA clears one copy while others may still read the previous hub's.
+// With `maj` (sweeps whose rows mostly keep their label) the cluster first
+// weighs the row's own label (own_weight_pass, barrier C, totals read from
+// all CTAs): a strict majority is Eq. 2's argmax, the label stays and the
+// table pass is skipped.
+// Every branch around a barrier depends only on values all CTAs of the
+// cluster read alike (the hub index from rank 0, the OR of the flags, the
+// majority totals).
+template <bool WEIGHTED, bool ASYNC>
+__global__ void __launch_bounds__(512, 2) hub_cluster_kernel(SweepArgs a, HubPlan hp, unsigned tb, int maj) {
+  extern __shared__ unsigned long long smem_c64[];
+  __shared__ BlockRowShared sh;
+  __shared__ int s_hub[2], s_ovf[2];
+  __shared__ unsigned long long s_mown[2], s_mtot[2];
+  __shared__ int s_skip[2];
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank();
+  const int nclu = (int)a.ctr->hub_clusters;
+  const int* __restrict__ work = a.work + a.ctr->cls_start[CLS_HUB];
+  const Pol pol = make_pol();
+  const SlotTable st = make_table(smem_c64, tb);
+  const int tid = (int)(rank * blockDim.x + threadIdx.x), nthr = HUB_CLUSTER * (int)blockDim.x;
+  for (int par = 0;; par ^= 1) {
+    for (unsigned k = threadIdx.x; k < tb; k += blockDim.x) {
+      st.keys[k] = EMPTY32;
+      st.sums[k] = 0;
+    }
+    if (threadIdx.x == 0) {
+      sh.ovf[par] = 0;
+      s_mown[par] = 0;
+      s_mtot[par] = 0;
+      if (rank == 0) s_hub[par] = (int)atomicAdd(&a.ctr->hub_clu_next, 1u);
+    }
+    cl.sync();   // A
+    const int q = *(volatile int*)cl.map_shared_rank(&s_hub[par], 0);
+    if (q >= nclu) break;
+    const int i = hp.clu[q];
+    const int v = work[i];
+    const long long s = a.off[v];
+    const int d = (int)(a.off[v + 1] - s);
+    const int own = own_label<ASYNC>(a, v);
+    const int* cp = a.col + s;
+    const int* wp = a.w + s;
+    const int* lp = a.lg ? a.lg + s : nullptr;
+    if (maj) {
+      unsigned own_w = 0, tot_w = 0;
+      own_weight_pass<WEIGHTED, ASYNC>(a, v, own, cp, wp, lp, d, tid, nthr, pol, own_w, tot_w);
+      const unsigned long long ow = warp_sum_u64(own_w), tw = warp_sum_u64(tot_w);
+      if ((threadIdx.x & 31) == 0) {
+        if (ow) atomicAdd(&s_mown[par], ow);
+        if (tw) atomicAdd(&s_mtot[par], tw);
+      }
+      cl.sync();   // C
+      if (threadIdx.x < 32) {
+        unsigned long long o = 0, t = 0;
+        if (threadIdx.x < HUB_CLUSTER) {
+          o = *(volatile unsigned long long*)cl.map_shared_rank(&s_mown[par], threadIdx.x);
+          t = *(volatile unsigned long long*)cl.map_shared_rank(&s_mtot[par], threadIdx.x);
+        }
+        o = warp_sum_u64(o);
+        t = warp_sum_u64(t);
+        if (threadIdx.x == 0) s_skip[par] = 2 * o > t;
+      }
+      __syncthreads();
+      if (s_skip[par]) continue;   // the label stays (hp.best 0, hp.own 0)
+    }
+    cluster_row<WEIGHTED, ASYNC, false>(a, v, own, cp, wp, lp, d, tid, nthr, st, tb, nullptr, 0, nullptr, nullptr, 0,
+                                        pol, sh, par, cl);
+    cl.sync();   // B
+    if (threadIdx.x < 32) {
+      const int f = threadIdx.x < HUB_CLUSTER ? *(volatile int*)cl.map_shared_rank(&sh.ovf[par], threadIdx.x) : 0;
+      const int any = __any_sync(FULL, f);
+      if (threadIdx.x == 0) s_ovf[par] = any;
+    }
+    __syncthreads();
+    if (!s_ovf[par]) {
+      unsigned long long b = 0;
+      for (unsigned k = threadIdx.x; k < tb; k += blockDim.x) {
+        const unsigned key = st.keys[k];
+        if (key != EMPTY32) {
+          const unsigned long long x = pack_key(st.sums[k], (int)key);
+          b = x > b ? x : b;
+        }
+      }
+      b = warp_max_u64(b);
+      if ((threadIdx.x & 31) == 0 && b) atomicMax(&sh.best[par], b);
+      __syncthreads();
+    } else {
+      cluster_row<WEIGHTED, ASYNC, true>(a, v, own, cp, wp, lp, d, tid, nthr, st, tb, hp.tab + 2 * hp.ustart[i],
+                                         (unsigned)(2 * d), hp.used + hp.ustart[i], hp.used_cnt + i,
+                                         2 * hp.ustart[i], pol, sh, par, cl);
+    }
+    if (threadIdx.x == 0) {
+      if (sh.best[par]) atomicMax(hp.best + i, sh.best[par]);
+      if (sh.own[par]) atomicAdd(hp.own + i, sh.own[par]);
+      if (WEIGHTED && a.check && sh.wsum[par]) atomicAdd(hp.wsum + i, sh.wsum[par]);
+    }
+  }
+  cl.sync();   // rank 0's s_hub stays readable until every CTA has read it
 }
 
 template <bool WEIGHTED, bool ASYNC>
@@ -203,30 +472,89 @@ __global__ void __launch_bounds__(256) hub_final_kernel(SweepArgs a, HubPlan hp,
 }
 
 namespace {
+// Clusters of the cluster kernel resident at once for the given table size
+// (0: such clusters cannot run); cached per size.
 template <bool W, bool A>
-cudaError_t launch_hub_t(const SweepArgs& a, const HubPlan& hp, const Tuning& t, const DeviceInfo& di,
-                         cudaStream_t s) {
+int cluster_slots(size_t smem) {
+  static size_t cached_smem = 0;
+  static int cached = 0;
+  if (cached_smem == smem) return cached;
+  cached_smem = smem;
+  cached = 0;
+  if (cudaFuncSetAttribute(hub_cluster_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      (HUB_CLUSTER > 8 &&
+       cudaFuncSetAttribute(hub_cluster_kernel<W, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+           cudaSuccess)) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = HUB_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(HUB_CLUSTER, 1, 1);
+  cfg.blockDim = dim3(512, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, hub_cluster_kernel<W, A>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cached = n;
+  return cached;
+}
+
+template <bool W, bool A>
+cudaError_t launch_hub_t(const SweepArgs& a, const HubPlan& hp, bool maj, const Tuning& t, const DeviceInfo& di,
+                         cudaStream_t s, int* kernels) {
   const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
   static size_t attr_smem = 0;
   if (attr_smem != smem) {
     cudaFuncSetAttribute(hub_piece_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_smem = smem;
   }
-  hub_plan_kernel<<<1, 1024, 0, s>>>(a, hp);
+  const int nclusters = t.hub_cluster_max > 0 ? cluster_slots<W, A>(smem) : 0;
+  hub_plan_kernel<<<1, 1024, 0, s>>>(a, hp, nclusters > 0 ? (long long)t.hub_cluster_max : 0ll);
+  int launches = 3;
+  if (nclusters > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = HUB_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(HUB_CLUSTER * (unsigned)nclusters, 1, 1);
+    cfg.blockDim = dim3(512, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, hub_cluster_kernel<W, A>, a, hp, (unsigned)t.blk_slots, maj ? 1 : 0);
+    if (e != cudaSuccess) return e;
+    ++launches;
+  }
   hub_piece_kernel<W, A><<<(int)block_grid_size(t, di), t.blk_block, smem, s>>>(a, hp, (unsigned)t.blk_slots);
   hub_final_kernel<A><<<2 * di.sm_count, 256, 0, s>>>(a, hp, W ? 1 : 0);
-  count_launches(3);
+  count_launches(launches);
+  *kernels = launches;
   return cudaGetLastError();
 }
 }  // namespace
 
 bool hub_pieces_fit(const Tuning& t) { return HUB_PIECE * 4 <= t.blk_slots * 3 - 4 * 512; }
 
-cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weighted, bool async_mode, const Tuning& t,
-                              const DeviceInfo& di, cudaStream_t s) {
+cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weighted, bool async_mode, bool majority,
+                              const Tuning& t, const DeviceInfo& di, cudaStream_t s, int* kernels) {
   if (weighted)
-    return async_mode ? launch_hub_t<true, true>(a, hp, t, di, s) : launch_hub_t<true, false>(a, hp, t, di, s);
-  return async_mode ? launch_hub_t<false, true>(a, hp, t, di, s) : launch_hub_t<false, false>(a, hp, t, di, s);
+    return async_mode ? launch_hub_t<true, true>(a, hp, majority, t, di, s, kernels)
+                      : launch_hub_t<true, false>(a, hp, majority, t, di, s, kernels);
+  return async_mode ? launch_hub_t<false, true>(a, hp, majority, t, di, s, kernels)
+                    : launch_hub_t<false, false>(a, hp, majority, t, di, s, kernels);
 }
 
 }  // namespace gsl

@@ -43,6 +43,7 @@ struct Tuning {
   int blk_block = 512;       // threads per block of the block kernel
   int pregather = 0;         // two-phase sweeps: 0 never, 1 when the frontier is large, 2 always
   int majority = 1;          // own-label majority pass: 0 never, 1 once labels settle, 2 always
+  int hub_cluster_max = 1 << 30;  // hubs up to this degree go to one thread-block cluster each (0: never)
 };
 
 // Degree bounds of the classes (see common.cuh).
@@ -122,11 +123,15 @@ struct HubPlan {
   unsigned* used_cnt;           // table slots claimed for hub i
   unsigned* used;               // their indices: hub i at used[ustart[i]..]
   unsigned long long* tab;      // hub i's table at tab[2 ustart[i] .. 2 ustart[i+1])
+  int* clu;                     // frontier hubs taken by clusters (indices i), hub_clusters of them
 };
 // True when a piece always fits the block kernel's shared table.
 bool hub_pieces_fit(const Tuning& t);
-cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weighted, bool async_mode, const Tuning& t,
-                              const DeviceInfo& di, cudaStream_t s);
+// Class 9: plan, cluster kernel (hubs up to t.hub_cluster_max; with
+// `majority`, rows whose own label holds a strict majority keep it without
+// a table), pieces, final pass.  *kernels = launches made.
+cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weighted, bool async_mode, bool majority,
+                              const Tuning& t, const DeviceInfo& di, cudaStream_t s, int* kernels);
 
 // float_kernels.cu: sweeps with float32 weights and float64 sums.  Classes
 // 6..9 use one block per row; rows whose 2 d slots exceed shared memory use

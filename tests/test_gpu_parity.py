@@ -375,14 +375,19 @@ def _giant_hubs(seed=4):
     return I.csr_from_pairs(n, np.concatenate(u), np.concatenate(v), name="sbm100k-giant-hubs")
 
 
+@pytest.mark.parametrize("clu", [None, 0, 36_000])
 @pytest.mark.parametrize("tuning", [None, (1024, 4096), (256, 8192), (32, 48)])
 @pytest.mark.parametrize("w", [False, True])
-def test_hub_pieces_bit_exact(gpu_lib, tuning, w):
-    """Class 9 runs in pieces of 8192 entries aggregated across blocks."""
+def test_hub_pieces_bit_exact(gpu_lib, tuning, w, clu):
+    """Class 9: rows up to the cluster bound (default every row; 0 = none;
+    36000 = some of each) in 8-CTA clusters, longer ones in pieces of 8192
+    entries aggregated across blocks."""
     c = gpu_lib.Context(0)
     if tuning:
         c.set_tuning(*tuning)
         c.set_majority(2)
+    if clu is not None:
+        c.set_hub_cluster(clu)
     for g0 in (_giant_hubs(), I.rmat(17, 24, seed=1)):
         g = weighted(g0, 5, 3) if w else g0
         assert np.diff(g.offsets).max() > 8192
@@ -397,6 +402,45 @@ def test_hub_pieces_bit_exact(gpu_lib, tuning, w):
         # async: invariants only
         lab = c.gsllpa(off, col, wt, mode=1).cpu().numpy()
         assert (lab <= np.arange(g.n)).all() and O.disconnected(g, lab)[0] == 0
+
+
+def _wide_hubs(seed=6):
+    """130,000-vertex planted partition plus hubs of 120,000, 90,000 and
+    40,000 distinct neighbours: from all-distinct labels the two largest
+    hold more labels than an 8-CTA cluster's shared tables (8 x 9216)."""
+    rng = np.random.default_rng(seed)
+    base = I.sbm_planted(130_000, 500, 10.0, 2.0, seed=seed)
+    src = np.repeat(np.arange(base.n), np.diff(base.offsets))
+    keep = src < base.cols
+    u, v = [src[keep]], [base.cols[keep]]
+    for h, deg in enumerate((120_000, 90_000, 40_000)):
+        nb = rng.choice(base.n, deg, replace=False)
+        u.append(np.full(nb.shape[0], base.n + h))
+        v.append(nb)
+    return I.csr_from_pairs(base.n + 3, np.concatenate(u), np.concatenate(v), name="sbm130k-wide-hubs")
+
+
+@pytest.mark.parametrize("w", [False, True])
+def test_hub_cluster_overflow_falls_back(gpu_lib, w):
+    """A cluster whose distributed table fills redoes the row in the hub's
+    global table: same labels as the oracle and as pieces alone."""
+    g0 = _wide_hubs()
+    g = weighted(g0, 5, 3) if w else g0
+    off, col, wt = dev(g)
+    rng = np.random.default_rng(7)
+    perms = [rng.permutation(g.n).astype(np.int32), rng.integers(0, 2000, g.n).astype(np.int32)]
+    for clu in (None, 0, 100_000):
+        c = gpu_lib.Context(0)
+        if clu is not None:
+            c.set_hub_cluster(clu)
+        for prev in perms:
+            got = c.lpa(off, col, wt, labels_init=torch.from_numpy(prev).to(DEV), tolerance=0.0, max_iters=1)
+            assert np.array_equal(got.cpu().numpy(), O.sync_sweep(g, prev)[0]), (clu, w)
+        got, st = c.lpa(off, col, wt, tolerance=0.0, max_iters=4, stats=True)
+        want, t, dn = O.lpa_sync(g, 0.0, 4)
+        assert st["changed"] == dn[:t].tolist() and np.array_equal(got.cpu().numpy(), want), (clu, w)
+    with pytest.raises(gpu_lib.GslError):
+        c.set_hub_cluster(-1)
 
 
 @pytest.mark.parametrize("shape", [(256, 6144), (128, 1024), (512, 4096), (256, 12288)])
