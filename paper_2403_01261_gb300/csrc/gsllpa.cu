@@ -395,6 +395,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     // almost as many distinct labels as neighbours (about 0.3 d on R-MAT
     // hubs): hubs beyond three shared tables' worth go to global tables
     a.gthresh = (t == 2 && !async_mode && !labels_init) ? 3 * c->tune.blk_slots : 0;
+    a.spread = (t == 2 && !async_mode && !labels_init) ? 1 : 0;
     // Sweep 1 changes every vertex that has a neighbour, and a sweep after
     // one that changed more than half of the vertices is run on all
     // vertices: marking would select nearly everything anyway.
@@ -720,6 +721,7 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
     a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
     const bool filter = !a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
     a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
+    a.spread = (t == 2 && !async_mode) ? 1 : 0;
     SweepArgs af = a;
     if (filter) {
       pe = prof ? prof_begin(c, cs) : -1;

@@ -246,7 +246,7 @@ __device__ __forceinline__ void cluster_row(const SweepArgs& a, int v, int own, 
                               : (unsigned)__popc(__ballot_sync(FULL, mine));
           if (mine) l[u] = -1;
           if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
-          const unsigned m = __match_any_sync(FULL, l[u]);
+          const unsigned m = label_group(l[u], a.spread);
           const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
           const bool leader = l[u] >= 0 && (m & lanemask_lt()) == 0;
           if (GLOBAL) {

@@ -31,6 +31,7 @@ struct SweepArgs {
   int check;                 // validate weights and weighted degrees
   int mark;                  // mark neighbours of changed vertices in fnext
   const int* lg;             // sync mode: labels gathered per entry, lg[e] = prev[col[e]] (null: gather)
+  int spread;                // labels read are nearly all distinct (sweep 2 from the identity labelling)
 };
 
 struct Tuning {

@@ -252,8 +252,8 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 // One warp aggregates the row (cp, wp, d) of vertex v into `tab` (cap
 // slots).  Four 32-entry chunks are loaded (columns, then labels) before any
 // is hashed, so each lane keeps eight loads in flight.  Within a chunk equal
-// labels are merged with __match_any_sync and only the lowest lane of each
-// group inserts.  Returns true (warp-uniform) once more than `limit`
+// labels are merged with __match_any_sync (label_group) and only the lowest
+// lane of each group inserts.  Returns true (warp-uniform) once more than `limit`
 // distinct labels have been inserted: the table is then abandoned.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
 __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
@@ -308,7 +308,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
                             : (unsigned)__popc(__ballot_sync(FULL, mine));
         if (mine) l[u] = -1;
         if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
-        const unsigned m = __match_any_sync(FULL, l[u]);
+        const unsigned m = label_group(l[u], a.spread);
         const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
         bool created = false;
         if (l[u] >= 0 && (m & lanemask_lt()) == 0) {

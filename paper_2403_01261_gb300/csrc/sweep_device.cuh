@@ -149,6 +149,15 @@ __device__ __forceinline__ unsigned slot_add(SlotTable t, unsigned cap, unsigned
   return 0;
 }
 
+// Lanes of a warp's chunk holding label l, merged so that one insert per
+// distinct label reaches the table.  When the labels read are nearly all
+// distinct (a.spread) the match costs more than it merges: every lane is
+// its own group.
+__device__ __forceinline__ unsigned label_group(int l, int spread) {
+  if (spread) return 1u << (threadIdx.x & 31);
+  return __match_any_sync(FULL, l);
+}
+
 }  // namespace
 
 // Per-row values shared by a block.  Rows alternate between two copies, so
@@ -290,7 +299,7 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
                               : (unsigned)__popc(__ballot_sync(FULL, mine));
           if (mine) l[u] = -1;
           if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
-          const unsigned m = __match_any_sync(FULL, l[u]);
+          const unsigned m = label_group(l[u], a.spread);
           const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
           bool created = false;
           if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
