@@ -94,9 +94,9 @@ int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
 
 /* Shape of the block kernel (degree warp_max+1..blk_max and hub pieces):
  * threads per block (128, 256 or 512) and shared-memory table slots per
- * block (8 bytes each; at least 4 * threads, so that the slots warps may
- * still claim after a table is declared full always fit, and the table
- * must fit one block's shared memory).  Defaults 512 and 12288.  Hub rows are split into pieces only
+ * block (8 bytes each; at least 16 * threads, so that the slots warps may
+ * still claim after a table is declared full -- up to 128 per warp -- fit
+ * in its last quarter, and the table must fit one block's shared memory).  Defaults 512 and 12288.  Hub rows are split into pieces only
  * while a piece always fits the table (at least ~11,600 slots); below that
  * hubs take one block each.  Results do not depend on these values. */
 int gsl_ctx_set_block_config(gsl_ctx* ctx, int32_t threads, int32_t table_slots);

@@ -922,8 +922,8 @@ int gsl_ctx_set_block_config(gsl_ctx* c, int32_t threads, int32_t table_slots) {
   if (threads != 128 && threads != 256 && threads != 512)
     return fail(c, GSL_ERR_INVALID, "block threads must be 128, 256 or 512");
   const long long bytes = (long long)table_slots * 8 + 1024;   // + the kernel's static shared memory
-  if (table_slots < 4 * threads || bytes > c->di.max_smem_optin)
-    return fail(c, GSL_ERR_INVALID, "table_slots must be >= 4 * threads and fit the shared memory of one block");
+  if (table_slots < 16 * threads || bytes > c->di.max_smem_optin)
+    return fail(c, GSL_ERR_INVALID, "table_slots must be >= 16 * threads and fit the shared memory of one block");
   c->tune.blk_block = threads;
   c->tune.blk_slots = table_slots;
   c->batch_key.clear();   // the captured batched loop used the old shape

@@ -473,7 +473,9 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
       int ovf = 1;
       if (!(gthresh > 0 && d > gthresh)) {
         const unsigned cap = want < tb ? want : tb;
-        // each of up to 16 warps may add 32 new slots after the flag is raised
+        // each warp may add up to 128 new slots (one round) after the flag is
+        // raised: at most 4 * threads, within the last quarter of a table of
+        // at least 16 * threads slots
         const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
         ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, lp, d, stab, cap, limit, pol, sh, par);
       }

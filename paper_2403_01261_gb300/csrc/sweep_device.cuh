@@ -226,9 +226,9 @@ __device__ __forceinline__ void block_publish(const SweepArgs& a, BlockRowShared
 // sh[par].  A round covers blockDim.x * 4 entries; chunk u of warp w in the
 // round starting at r0 holds entries r0 + (u * warps + w) * 32 + lane, so a
 // row shorter than a round still spreads over every warp.  With a finite
-// `limit` (shared table), a warp checks the overflow flag before each chunk
-// and adds its new slots to the block's count after it; past `limit` the
-// flag is raised and the row is abandoned.  Returns the flag (block-uniform
+// `limit` (shared table), a warp checks the overflow flag before each round
+// and adds its new slots (at most 128) to the block's count after it; past
+// `limit` the flag is raised and the row is abandoned.  Returns the flag (block-uniform
 // after the closing barrier).  The global-table pass (limit infinite) leaves
 // the flag alone, so every thread still reads the value that sent it there.
 template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
@@ -286,35 +286,30 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
 #pragma unroll
       for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, r0 + 2 * step + cb + u * cu, pol, jn[u], wn[u]);
     }
-    bool stop = false;
+    const bool counted = !GLOBAL && limit != 0xFFFFFFFFu;
+    if (counted && __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sh.ovf[par] : 0, 0)) break;   // warp-uniform
+    unsigned created_round = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (!stop && r0 + (u * nw + wid) * 32 < d) {   // warp-uniform
-        if (!GLOBAL && limit != 0xFFFFFFFFu &&
-            __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sh.ovf[par] : 0, 0)) {
-          stop = true;
-        } else {
-          const bool mine = l[u] == own;
-          own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
-                              : (unsigned)__popc(__ballot_sync(FULL, mine));
-          if (mine) l[u] = -1;
-          if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
-          const unsigned m = label_group(l[u], a.spread);
-          const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
-          bool created = false;
-          if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
-            const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
-            const unsigned long long k = pack_key(sum, l[u]);
-            best = k > best ? k : best;
-          }
-          if (!GLOBAL && limit != 0xFFFFFFFFu) {
-            const unsigned nc = __popc(__ballot_sync(FULL, created));
-            if (lane == 0 && nc && atomicAdd(&sh.used[par], nc) + nc > limit) *(volatile int*)&sh.ovf[par] = 1;
-          }
+      if (r0 + (u * nw + wid) * 32 < d) {   // warp-uniform
+        const bool mine = l[u] == own;
+        own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
+                            : (unsigned)__popc(__ballot_sync(FULL, mine));
+        if (mine) l[u] = -1;
+        if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
+        const unsigned m = label_group(l[u], a.spread);
+        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+        bool created = false;
+        if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+          const unsigned long long k = pack_key(sum, l[u]);
+          best = k > best ? k : best;
         }
+        if (counted) created_round += __popc(__ballot_sync(FULL, created));
       }
     }
-    if (stop) break;
+    if (counted && lane == 0 && created_round && atomicAdd(&sh.used[par], created_round) + created_round > limit)
+      *(volatile int*)&sh.ovf[par] = 1;
   }
   block_publish<WEIGHTED>(a, sh, par, best, wsum, own_sum);
   __syncthreads();
