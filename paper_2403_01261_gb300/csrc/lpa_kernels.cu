@@ -299,14 +299,27 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
 #pragma unroll
       for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 256 + 32 * u + lane, pol, jn[u], wn[u]);
     }
+    if (!WEIGHTED) {
+      // entries carrying the vertex's own label are counted in registers,
+      // the round's four chunks first: once they are more than half of the
+      // row's d entries no other label can reach their count, and the rest
+      // of the row is not needed (after sweep 1, which reads every entry)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool mine = l[u] == own;
+        own_sum += (unsigned)__popc(__ballot_sync(FULL, mine));
+        if (mine) l[u] = -1;
+      }
+      if (!a.check && 2u * own_sum > (unsigned)d) return false;
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
-        // entries carrying the vertex's own label are summed in registers
-        const bool mine = l[u] == own;
-        own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
-                            : (unsigned)__popc(__ballot_sync(FULL, mine));
-        if (mine) l[u] = -1;
+        if (WEIGHTED) {   // own-label weights summed in registers
+          const bool mine = l[u] == own;
+          own_sum += __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u);
+          if (mine) l[u] = -1;
+        }
         if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
         const unsigned m = label_group(l[u], a.spread);
         const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
@@ -513,6 +526,46 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
 }
 
 // ---------------------------------------------------------------------------
+// The filter's pass over one row, one warp (own_weight_pass with 32
+// threads): with unit weights it stops as soon as the own label holds more
+// than half of the row's d entries, since it then holds a strict majority
+// of the whole row whatever the rest carries (`early`).  Returns the
+// entries read.
+template <bool WEIGHTED, bool ASYNC>
+__device__ __forceinline__ int filter_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
+                                          const int* lp, int d, const Pol& pol, unsigned& own_w, unsigned& tot_w,
+                                          bool& early) {
+  const int lane = threadIdx.x & 31;
+  int jn[4], wn[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, lane + 32 * u, pol, jn[u], wn[u]);
+  for (int r0 = 0; r0 < d; r0 += 128) {
+    int l[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      l[u] = entry_label<ASYNC>(a, lp, r0 + lane + 32 * u, jn[u], v, pol);
+      w[u] = wn[u];
+    }
+    const bool more = r0 + 128 < d;   // warp-uniform
+    if (more) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, r0 + 128 + lane + 32 * u, pol, jn[u], wn[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (l[u] >= 0) {
+        tot_w += (unsigned)w[u];
+        if (l[u] == own) own_w += (unsigned)w[u];
+      }
+    }
+    if (!WEIGHTED && more && 2u * __reduce_add_sync(FULL, own_w) > (unsigned)d) {
+      early = true;
+      return r0 + 128;
+    }
+  }
+  return d;
+}
+
 // Own-label majority filter for classes 7 and 8 (rows of 257..blk_max
 // entries by default: long enough that one extra lean pass costs less than
 // a table), run before their table kernels once labels have started to
@@ -541,17 +594,18 @@ __global__ void __launch_bounds__(256) majority_filter_kernel(SweepArgs a, int* 
     const int d = (int)(a.off[v + 1] - s);
     const int old = own_label<ASYNC>(a, v);
     unsigned ow = 0, tw = 0;
-    own_weight_pass<WEIGHTED, ASYNC>(a, v, old, a.col + s, a.w + s, a.lg ? a.lg + s : nullptr, d, lane, 32, pol, ow,
-                                     tw);
+    bool early = false;
+    const int read = filter_row<WEIGHTED, ASYNC>(a, v, old, a.col + s, a.w + s, a.lg ? a.lg + s : nullptr, d, pol, ow,
+                                                 tw, early);
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       ow += __shfl_xor_sync(FULL, ow, o);
       tw += __shfl_xor_sync(FULL, tw, o);
     }
     if (lane == 0) {
-      if (2ull * ow > (unsigned long long)tw) {
+      if (early || 2ull * ow > (unsigned long long)tw) {
         store_label<ASYNC>(a, v, old, false);
-        my_scan += (unsigned long long)d;
+        my_scan += (unsigned long long)read;
         my_settled += 1;
       } else {
         out[start + atomicAdd(&a.ctr->uns_count[cls], 1u)] = v;
