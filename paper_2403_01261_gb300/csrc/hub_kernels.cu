@@ -270,6 +270,53 @@ __device__ __forceinline__ void cluster_row(const SweepArgs& a, int v, int own, 
   __syncthreads();
 }
 
+// The cluster's own-label pass over a hub row (own_weight_pass over the
+// cluster's virtual threads).  With unit weights each warp adds its round's
+// own-label count to rank 0's counter `cnt` and stops once the returned
+// total is more than half of the row's d entries: the own label then holds a
+// strict majority whatever the rest carries.
+template <bool WEIGHTED, bool ASYNC>
+__device__ __forceinline__ void cluster_own_pass(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
+                                                 const int* lp, int d, int tid, int nthr, const Pol& pol,
+                                                 unsigned& own_w, unsigned& tot_w, unsigned* cnt) {
+  const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+  const int step = nw * 128;
+  const int cb = wid * 32 + lane, cu = nw * 32;
+  int jn[4], wn[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, cb + u * cu, pol, jn[u], wn[u]);
+  for (int r0 = 0; r0 < d; r0 += step) {
+    int l[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      l[u] = entry_label<ASYNC>(a, lp, r0 + cb + u * cu, jn[u], v, pol);
+      w[u] = wn[u];
+    }
+    const bool more = r0 + step < d;   // cluster-uniform
+    if (more) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, r0 + step + cb + u * cu, pol, jn[u], wn[u]);
+    }
+    unsigned o = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (l[u] >= 0) {
+        tot_w += (unsigned)w[u];
+        if (l[u] == own) {
+          own_w += (unsigned)w[u];
+          ++o;
+        }
+      }
+    }
+    if (!WEIGHTED && more) {
+      o = __reduce_add_sync(FULL, o);
+      unsigned total = 0;
+      if (lane == 0 && o) total = atomicAdd(cnt, o) + o;
+      if (2u * __shfl_sync(FULL, total, 0) > (unsigned)d) return;
+    }
+  }
+}
+
 // Hubs of degree <= cmax (listed by the plan kernel), one thread-block
 // cluster at a time: rank 0 takes the next hub from a counter, the row is
 // aggregated in the CTAs' shared tables (cluster_row), each CTA scans its
@@ -296,6 +343,7 @@ __global__ void __launch_bounds__(512, 2) hub_cluster_kernel(SweepArgs a, HubPla
   __shared__ BlockRowShared sh;
   __shared__ int s_hub[2], s_ovf[2];
   __shared__ unsigned long long s_mown[2], s_mtot[2];
+  __shared__ unsigned s_mcnt[2];   // rank 0's: own-label entries counted so far (unit weights)
   __shared__ int s_skip[2];
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
@@ -313,6 +361,7 @@ __global__ void __launch_bounds__(512, 2) hub_cluster_kernel(SweepArgs a, HubPla
       sh.ovf[par] = 0;
       s_mown[par] = 0;
       s_mtot[par] = 0;
+      s_mcnt[par] = 0;
       if (rank == 0) s_hub[par] = (int)atomicAdd(&a.ctr->hub_clu_next, 1u);
     }
     cl.sync();   // A
@@ -328,7 +377,8 @@ __global__ void __launch_bounds__(512, 2) hub_cluster_kernel(SweepArgs a, HubPla
     const int* lp = a.lg ? a.lg + s : nullptr;
     if (maj) {
       unsigned own_w = 0, tot_w = 0;
-      own_weight_pass<WEIGHTED, ASYNC>(a, v, own, cp, wp, lp, d, tid, nthr, pol, own_w, tot_w);
+      cluster_own_pass<WEIGHTED, ASYNC>(a, v, own, cp, wp, lp, d, tid, nthr, pol, own_w, tot_w,
+                                        cl.map_shared_rank(&s_mcnt[par], 0));
       const unsigned long long ow = warp_sum_u64(own_w), tw = warp_sum_u64(tot_w);
       if ((threadIdx.x & 31) == 0) {
         if (ow) atomicAdd(&s_mown[par], ow);
@@ -343,7 +393,9 @@ __global__ void __launch_bounds__(512, 2) hub_cluster_kernel(SweepArgs a, HubPla
         }
         o = warp_sum_u64(o);
         t = warp_sum_u64(t);
-        if (threadIdx.x == 0) s_skip[par] = 2 * o > t;
+        // a strict majority of the row, or (unit weights, the pass stopped
+        // early) more than half of its d entries
+        if (threadIdx.x == 0) s_skip[par] = 2 * o > t || (!WEIGHTED && 2 * o > (unsigned long long)d);
       }
       __syncthreads();
       if (s_skip[par]) continue;   // the label stays (hp.best 0, hp.own 0)
