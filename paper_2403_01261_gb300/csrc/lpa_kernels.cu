@@ -337,13 +337,15 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
   return false;
 }
 
-// Classes 6 and 7: one warp per vertex, TW slots of shared memory per warp.
+// Classes 6 and 7: one warp per vertex, TW slots of shared memory per warp
+// (class 6: four 256-thread blocks per SM, registers capped to fit; class
+// 7's 8 KB tables allow three).
 // With SPILL, a vertex whose labels overflow the shared table is redone in
 // the warp's region of the global fallback tables (2 * warp_max slots);
 // without it the class bound guarantees 2 d <= TW.  The next vertex's
 // worklist entry and offsets are loaded while the current one is processed.
 template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL>
-__global__ void __launch_bounds__(256, 3) sweep_warp_kernel(SweepArgs a, int cls) {
+__global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(SweepArgs a, int cls) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_w64[];
   const int lane = threadIdx.x & 31;
@@ -569,15 +571,15 @@ __device__ __forceinline__ int filter_row(const SweepArgs& a, int v, int own, co
 // Own-label majority filter for classes 7 and 8 (rows of 257..blk_max
 // entries by default: long enough that one extra lean pass costs less than
 // a table), run before their table kernels once labels have started to
-// settle.  One warp per row, no shared memory (so full occupancy and many
-// rows in flight): the weight of the row's entries carrying the vertex's
+// settle.  One warp per row, no shared memory and registers capped for six
+// 256-thread blocks per SM (many rows in flight): the weight of the row's entries carrying the vertex's
 // own label is compared with the row's total (the vertex itself excluded).
 // A strict majority is Eq. 2's argmax: the label stays and the row is done.
 // Other rows are appended to `out` at their class's region and counted in
 // Counters::uns_count; filter_counts_kernel then makes those the class
 // counts for the table kernels.
 template <bool WEIGHTED, bool ASYNC>
-__global__ void __launch_bounds__(256) majority_filter_kernel(SweepArgs a, int* __restrict__ out) {
+__global__ void __launch_bounds__(256, 6) majority_filter_kernel(SweepArgs a, int* __restrict__ out) {
   if (stopped(a)) return;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
