@@ -124,6 +124,12 @@ int gsl_ctx_set_majority(gsl_ctx* ctx, int32_t mode);
  * statistics do not depend on the mode. */
 int gsl_ctx_set_pregather(gsl_ctx* ctx, int32_t mode);
 
+/* Float-weight sweeps (gsl_lpa_f32, gsl_gsllpa_f32): 1 (default) runs them
+ * on the integer path when the weights have the exact fixed-point form
+ * described at gsl_lpa_f32, 0 always sums in float64.  Other values:
+ * GSL_ERR_INVALID.  Labels do not depend on it. */
+int gsl_ctx_set_f32_fixed(gsl_ctx* ctx, int32_t mode);
+
 /* Hub rows (synchronous or asynchronous sweeps, integer weights) whose
  * degree is at most max_degree are aggregated by one thread-block cluster
  * of 8 CTAs each: the row's label table is spread over the 8 CTAs' shared
@@ -197,7 +203,12 @@ int gsl_lpa(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, const int32_
  * not guaranteed bit-identical to a sequential evaluation where two sums
  * agree to rounding; they are whenever every partial sum is exact in
  * float64 (for instance small integers or multiples of 1/8).  Modularity is
- * formed from float64 sums. */
+ * formed from float64 sums.  When every weight is a multiple of 2^-S and
+ * every row's total times 2^S stays below 2^31 (checked through the largest
+ * weight and the largest degree), every float64 sum is exact and the
+ * sweeps run on the integer path with weights w * 2^S, which compares the
+ * same sums scaled by 2^S: the labels are the float path's
+ * (gsl_ctx_set_f32_fixed turns this off). */
 int gsl_lpa_f32(gsl_ctx* ctx, const gsl_csr* g, const float* weights, const int32_t* labels_init,
                 double tolerance, int32_t max_iters, int32_t mode, int32_t* labels_out, gsl_stats* stats,
                 void* stream);

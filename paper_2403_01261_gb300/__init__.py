@@ -120,6 +120,7 @@ def load():
         lib.gsl_ctx_set_block_config.argtypes = [P, i32, i32]
         lib.gsl_ctx_set_majority.argtypes = [P, i32]
         lib.gsl_ctx_set_hub_cluster.argtypes = [P, i64]
+        lib.gsl_ctx_set_f32_fixed.argtypes = [P, i32]
         lib.gsl_lpa_f32.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_gsllpa_f32.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
         lib.gsl_modularity_f32.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
@@ -230,6 +231,11 @@ class Context:
     def set_majority(self, mode: int):
         """0: never, 1: once labels settle (default), 2: every sweep after the first."""
         self._raise(self._lib.gsl_ctx_set_majority(self._h, int(mode)))
+
+    def set_f32_fixed(self, mode: int):
+        """1 (default): float weights with an exact fixed-point form run on
+        the integer sweeps; 0: always float64 sums."""
+        self._raise(self._lib.gsl_ctx_set_f32_fixed(self._h, int(mode)))
 
     def set_hub_cluster(self, max_degree: int):
         """Hubs up to this degree are aggregated by one 8-CTA thread-block

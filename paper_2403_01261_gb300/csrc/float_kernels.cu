@@ -529,4 +529,66 @@ cudaError_t launch_modularity_f32(const long long* off, const int* col, const fl
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Exact fixed-point form of float32 weights.  A finite positive float32 is
+// m * 2^q with an integer m < 2^24; if every weight of the graph is a
+// multiple of 2^-S (S = -min q) and every row's total times 2^S stays below
+// 2^31, then w * 2^S are int32 values whose integer row sums are exact, and
+// so are the float64 sums of the float path (every partial sum is a
+// multiple of 2^-S below 2^31-S, well inside float64's 53 bits).  Both
+// paths then compare the same numbers scaled by 2^S, so the integer sweeps
+// give the float path's labels.
+//
+// out[0] = 1024 + min over weights of q (exponent of the lowest set bit),
+// out[1] = 1024 + max over weights of the exponent of the highest set bit,
+// out[2] = 1 if a weight is not finite and positive or is subnormal.
+__global__ void __launch_bounds__(256) f32_exact_scan_kernel(const float* __restrict__ w, long long nnz,
+                                                             int* __restrict__ out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int lo = 1 << 30, hi = -(1 << 30), bad = 0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const unsigned b = __float_as_uint(__ldcs(w + e));
+    const unsigned ex = (b >> 23) & 0xFFu;
+    if ((b >> 31) || ex == 0 || ex == 0xFFu) {   // negative, zero, subnormal, inf or nan
+      bad = 1;
+      continue;
+    }
+    const unsigned m = (b & 0x7FFFFFu) | 0x800000u;
+    const int q = (int)ex - 150 + (__ffs(m) - 1);
+    lo = q < lo ? q : lo;
+    hi = (int)ex - 127 > hi ? (int)ex - 127 : hi;
+  }
+  lo = __reduce_min_sync(FULL, lo);
+  hi = __reduce_max_sync(FULL, hi);
+  bad = __reduce_or_sync(FULL, (unsigned)bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (lo != (1 << 30)) atomicMin(out, 1024 + lo);
+    if (hi != -(1 << 30)) atomicMax(out + 1, 1024 + hi);
+    if (bad) atomicOr(out + 2, 1);
+  }
+}
+
+__global__ void __launch_bounds__(256) f32_to_fixed_kernel(const float* __restrict__ w, long long nnz, int shift,
+                                                           int* __restrict__ wi) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const float scale = __int_as_float((127 + shift) << 23);   // 2^shift: the products are exact
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+    __stcs(wi + e, (int)(__ldcs(w + e) * scale));
+}
+
+cudaError_t launch_f32_exact_scan(const float* w, long long nnz, int* out, const DeviceInfo& di, cudaStream_t s) {
+  cudaMemsetAsync(out, 0x7F, sizeof(int), s);           // a large minimum to start from
+  cudaMemsetAsync(out + 1, 0, 2 * sizeof(int), s);
+  f32_exact_scan_kernel<<<8 * di.sm_count, 256, 0, s>>>(w, nnz, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_fixed(const float* w, long long nnz, int shift, int* wi, const DeviceInfo& di,
+                                cudaStream_t s) {
+  f32_to_fixed_kernel<<<8 * di.sm_count, 256, 0, s>>>(w, nnz, shift, wi);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace gsl

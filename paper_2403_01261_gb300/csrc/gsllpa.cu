@@ -82,6 +82,12 @@ struct gsl_ctx {
   long long cap_st_w = 0;
   int* st_lab = nullptr;
   long long cap_st_lab = 0;
+  // float weights in exact fixed point (run on the integer sweeps)
+  int f32_fixed = 1;                    // 0: always float64 sums; 1: fixed point when exact
+  int* fix_w = nullptr;
+  long long cap_fix_w = 0;
+  int* fix_dev = nullptr;               // 3 ints
+  int* fix_h = nullptr;                 // pinned mirror
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
@@ -534,6 +540,9 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
       CK(launch_ident_stream_f32(OFF(g), n, g->cols, wf, g->nnz, c->rowbits, c->flag[1], c->lab[1], c->ctr, c->di,
                                  s));
       prof_end(c, pe, SL_IDENT, s, 3);
+      c->profile.slot[SL_IDENT].vertices += n;
+      c->profile.slot[SL_IDENT].entries += g->nnz;
+      c->profile.slot[SL_IDENT].bytes += 8.0 * (double)g->nnz + 16.0 * (double)n;   // columns, weights
       all_active = false;
     }
     {
@@ -553,7 +562,25 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
     }
     CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (c->prof) prof_resolve(c);
+    if (c->prof) {
+      prof_resolve(c);
+      // algorithmic bytes as in run_lpa: per processed vertex offsets,
+      // worklist entry, own label and label write; per entry the column, the
+      // neighbour's label and the float weight
+      long long act_all = 0;
+      for (int k = 0; k < NCLASS; ++k) {
+        auto& sl = c->profile.slot[SL_SWEEP0 + k];
+        const long long v = c->ctr_h->cls_count[k];
+        const long long e = (long long)c->ctr_h->cls_scanned[k];
+        sl.vertices += v;
+        sl.entries += e;
+        sl.bytes += 20.0 * (double)v + 12.0 * (double)e;
+        act_all += v;
+      }
+      auto& sb = c->profile.slot[SL_BIN];
+      sb.vertices += all_active ? n : act_all;
+      sb.bytes += (all_active ? 0.0 : (double)n) + 16.0 * (double)(all_active ? n : act_all) + 4.0 * (double)act_all;
+    }
     if (int r = map_err(c, c->ctr_h->err, "lpa_f32")) return r;
     const long long dn = (long long)c->ctr_h->dn;
     long long act = (long long)c->ctr_h->fast_active;
@@ -576,6 +603,33 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
     st->edges_scanned = scanned;
   }
   *final = async_mode ? c->lab[0] : c->lab[t & 1];
+  return GSL_OK;
+}
+
+// Float weights that are all multiples of 2^-S with every row total below
+// 2^(31-S) (checked through the largest weight and the largest degree) are
+// converted to int32 w * 2^S (float_kernels.cu): the integer sweeps then
+// compare the float path's exact float64 sums scaled by 2^S, so they give
+// its labels.  Sets *wi to the converted weights, or leaves it NULL (float
+// path) when the weights do not qualify or the context's mode is 0; invalid
+// weights are left to the float path, which reports them.  After
+// prepare_graph(g).
+int f32_fixed_point(gsl_ctx* c, const gsl_csr* g, const float* w, cudaStream_t s, int** wi) {
+  *wi = nullptr;
+  if (c->f32_fixed == 0 || g->nnz == 0) return GSL_OK;
+  CK(launch_f32_exact_scan(w, g->nnz, c->fix_dev, c->di, s));
+  CK(cudaMemcpyAsync(c->fix_h, c->fix_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c->fix_h[2]) return GSL_OK;
+  const int lo = c->fix_h[0] - 1024, hi = c->fix_h[1] - 1024;
+  const int shift = lo < 0 ? -lo : 0;
+  int dbits = 0;   // ceil(log2(largest degree))
+  while ((1ll << dbits) < c->ctr_h->max_degree) ++dbits;
+  // a weight is below 2^(hi+1), so a row total times 2^shift is below 2^(hi+1+shift+dbits)
+  if (shift > 30 || hi + 1 + shift + dbits > 31) return GSL_OK;
+  if (int r = grow(c, c->fix_w, c->cap_fix_w, g->nnz)) return r;
+  CK(launch_f32_to_fixed(w, g->nnz, shift, c->fix_w, c->di, s));
+  *wi = c->fix_w;
   return GSL_OK;
 }
 
@@ -780,7 +834,9 @@ int gsl_ctx_create(gsl_ctx** out, int device) {
             cudaMalloc(&c->sums, sizeof(ModSums)) == cudaSuccess &&
             cudaMallocHost(&c->sums_h, sizeof(ModSums)) == cudaSuccess &&
             cudaMalloc(&c->k_dev, sizeof(unsigned long long)) == cudaSuccess &&
-            cudaMallocHost(&c->k_h, sizeof(unsigned long long)) == cudaSuccess;
+            cudaMallocHost(&c->k_h, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&c->fix_dev, 3 * sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&c->fix_h, 3 * sizeof(int)) == cudaSuccess;
   for (int i = 0; ok && i < 4; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -799,12 +855,13 @@ int gsl_ctx_destroy(gsl_ctx* c) {
                    c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->work2, c->fkeys, c->fvals, c->hub_piece_start,
                    c->hub_ustart, c->hub_best, c->hub_own, c->hub_wsum, c->hub_used_cnt, c->hub_clu, c->hub_used, c->hub_tab,
                    c->ctr, c->sums, c->k_dev,
-                   c->st_off, c->st_col, c->st_w, c->st_lab};
+                   c->st_off, c->st_col, c->st_w, c->st_lab, c->fix_w, c->fix_dev};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (c->ctr_h) cudaFreeHost(c->ctr_h);
   if (c->sums_h) cudaFreeHost(c->sums_h);
   if (c->k_h) cudaFreeHost(c->k_h);
+  if (c->fix_h) cudaFreeHost(c->fix_h);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->evpool) cudaEventDestroy(e);
@@ -938,6 +995,13 @@ int gsl_ctx_set_majority(gsl_ctx* c, int32_t mode) {
   return GSL_OK;
 }
 
+int gsl_ctx_set_f32_fixed(gsl_ctx* c, int32_t mode) {
+  if (!c) return GSL_ERR_INVALID;
+  if (mode < 0 || mode > 1) return fail(c, GSL_ERR_INVALID, "f32 fixed-point mode must be 0 or 1");
+  c->f32_fixed = mode;
+  return GSL_OK;
+}
+
 int gsl_ctx_set_hub_cluster(gsl_ctx* c, int64_t max_degree) {
   if (!c) return GSL_ERR_INVALID;
   if (max_degree < 0) return fail(c, GSL_ERR_INVALID, "hub cluster degree must be >= 0");
@@ -1014,8 +1078,14 @@ int gsl_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* weights, const int32_
   if (int r = ensure_vertex_scratch(c, g->n)) return r;
   CK(cudaEventRecord(c->ev[0], s));
   if (int r = prepare_graph(c, g, s)) return r;
+  int* wi = nullptr;
+  if (int r = f32_fixed_point(c, g, weights, s, &wi)) return r;
   int* fin = nullptr;
-  if (int r = run_lpa_f32(c, g, weights, labels_init, tol, max_iters, mode, st, s, &fin)) return r;
+  if (wi) {
+    if (int r = run_lpa(c, g, wi, labels_init, tol, max_iters, mode, st, s, &fin)) return r;
+  } else {
+    if (int r = run_lpa_f32(c, g, weights, labels_init, tol, max_iters, mode, st, s, &fin)) return r;
+  }
   CK(cudaMemcpyAsync(labels_out, fin, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
   CK(cudaEventRecord(c->ev[1], s));
   CK(cudaEventSynchronize(c->ev[1]));
@@ -1036,8 +1106,14 @@ int gsl_gsllpa_f32(gsl_ctx* c, const gsl_csr* g, const float* weights, double to
   if (int r = ensure_vertex_scratch(c, g->n)) return r;
   CK(cudaEventRecord(c->ev[0], s));
   if (int r = prepare_graph(c, g, s)) return r;
+  int* wi = nullptr;
+  if (int r = f32_fixed_point(c, g, weights, s, &wi)) return r;
   int* fin = nullptr;
-  if (int r = run_lpa_f32(c, g, weights, nullptr, tol, max_iters, mode, st, s, &fin)) return r;
+  if (wi) {
+    if (int r = run_lpa(c, g, wi, nullptr, tol, max_iters, mode, st, s, &fin)) return r;
+  } else {
+    if (int r = run_lpa_f32(c, g, weights, nullptr, tol, max_iters, mode, st, s, &fin)) return r;
+  }
   CK(cudaEventRecord(c->ev[1], s));
   long long k = 0;
   if (int r = run_split(c, g, fin, labels_out, 0, &k, s)) return r;

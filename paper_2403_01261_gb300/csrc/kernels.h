@@ -141,6 +141,12 @@ cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weight
 long long float_table_blocks(const DeviceInfo& di);
 cudaError_t launch_sweep_f32(const SweepArgs& a, const float* wf, int cls, bool async_mode, unsigned* gkeys,
                              double* gvals, long long region, const DeviceInfo& di, cudaStream_t s);
+// Exact fixed-point form of float weights (float_kernels.cu): out[0..2] =
+// 1024 + lowest set-bit exponent, 1024 + highest set-bit exponent, invalid
+// flag; then wi[e] = w[e] * 2^shift.
+cudaError_t launch_f32_exact_scan(const float* w, long long nnz, int* out, const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_f32_to_fixed(const float* w, long long nnz, int shift, int* wi, const DeviceInfo& di,
+                                cudaStream_t s);
 // Eq. 1 with float weights: sums[0] = 2m, sums[1] = S1, sums[2] = S2 (sigma: n doubles).
 cudaError_t launch_modularity_f32(const long long* off, const int* col, const float* wf, const int* labels,
                                   long long n, double* sigma, double* sums, Counters* ctr, const DeviceInfo& di,

@@ -51,10 +51,27 @@ def graph(request):
 
 @pytest.fixture(scope="module")
 def ctxs(gpu_lib):
-    a = gpu_lib.Context(0)
-    b = gpu_lib.Context(0)
-    b.set_tuning(32, 48)
-    return [a, b]
+    """Default context, small class bounds, and both again with the float64
+    path forced (no fixed-point form of exact weights)."""
+    out = []
+    for fixed in (1, 0):
+        a = gpu_lib.Context(0)
+        b = gpu_lib.Context(0)
+        b.set_tuning(32, 48)
+        for c in (a, b):
+            c.set_f32_fixed(fixed)
+        out += [a, b]
+    return out
+
+
+def _took_integer_path(c, fn):
+    """Runs fn() with profiling on; the integer sweep loop profiles its label
+    initialisation, the float loop does not."""
+    c.set_profiling(True)
+    fn()
+    prof = {p["name"]: p for p in c.profile()}
+    c.set_profiling(False)
+    return prof["init_labels"]["launches"] > 0
 
 
 def test_dyadic_weights_bit_exact(graph, ctxs):
@@ -70,6 +87,32 @@ def test_dyadic_weights_bit_exact(graph, ctxs):
         assert np.array_equal(lab.cpu().numpy(), want_split)
         q = c.modularity_f32(off, col, lab, w)
         assert abs(q - O.modularity_f64(graph, wf, want_split)) <= 1e-9 * max(1.0, abs(q))
+
+
+def test_fine_dyadic_weights_fixed_point(gpu_lib, ctxs):
+    """Weights 1 + k / 2^20: multiples of 2^-20 whose row totals stay far
+    below 2^11, so every float64 sum is exact and the weights run on the
+    integer sweeps as w * 2^20; the labels equal the oracle's and the
+    float64 path's."""
+    rng = np.random.default_rng(21)
+    for g in (I.sbm_planted(), I.rmat(12, 8, seed=5)):
+        src = np.repeat(np.arange(g.n), np.diff(g.offsets))
+        key = np.minimum(src, g.cols).astype(np.int64) * g.n + np.maximum(src, g.cols)
+        uniq, inv = np.unique(key, return_inverse=True)
+        wf = (1.0 + rng.integers(0, 1 << 20, uniq.shape[0]) / float(1 << 20))[inv].astype(np.float32)
+        off, col, w = dev(g, wf)
+        want, t, dn = O.lpa_sync_f32(g, wf, 0.05, 20)
+        for c in ctxs:
+            got, st = c.lpa_f32(off, col, w, stats=True)
+            assert np.array_equal(got.cpu().numpy(), want) and st["changed"] == dn.tolist(), g.name
+        assert _took_integer_path(ctxs[0], lambda: ctxs[0].lpa_f32(off, col, w))
+        assert not _took_integer_path(ctxs[2], lambda: ctxs[2].lpa_f32(off, col, w))
+    # arbitrary floats (lowest bits down to 2^-30, values up to 3): float64 path
+    g = I.sbm_planted(2000, 100, 12.0, 3.0, seed=2)
+    off, col, w = dev(g, float_weights(g, 11, dyadic=False))
+    assert not _took_integer_path(ctxs[0], lambda: ctxs[0].lpa_f32(off, col, w))
+    with pytest.raises(gpu_lib.GslError):
+        ctxs[0].set_f32_fixed(2)
 
 
 def test_integer_valued_float_weights_equal_int32_path(graph, ctxs):
@@ -105,7 +148,7 @@ def test_float_pipeline_invariants_sync_and_async(graph, ctxs):
     wf = float_weights(graph, 7, dyadic=False)
     off, col, w = dev(graph, wf)
     for mode in (0, 1):
-        lab = ctxs[0].gsllpa_f32(off, col, w, mode=mode).cpu().numpy()
+        lab = ctxs[mode * 2].gsllpa_f32(off, col, w, mode=mode).cpu().numpy()
         v = np.arange(graph.n)
         assert (lab <= v).all() and np.array_equal(lab[lab], lab)
         assert O.disconnected(graph, lab)[0] == 0
@@ -119,8 +162,9 @@ def test_bad_float_weights_are_rejected(gpu_lib, ctxs):
         wf = np.ones(g.nnz, dtype=np.float32)
         wf[2] = bad
         off, col, w = dev(g, wf)
-        with pytest.raises(gpu_lib.GslError):
-            ctxs[0].lpa_f32(off, col, w)
+        for c in (ctxs[0], ctxs[2]):
+            with pytest.raises(gpu_lib.GslError):
+                c.lpa_f32(off, col, w)
         with pytest.raises(gpu_lib.GslError):
             ctxs[0].modularity_f32(off, col, torch.zeros(6, dtype=torch.int32, device=DEV), w)
     off, col, w = dev(g, np.ones(g.nnz, dtype=np.float32))
