@@ -82,6 +82,8 @@ struct gsl_ctx {
   long long cap_st_w = 0;
   int* st_lab = nullptr;
   long long cap_st_lab = 0;
+  unsigned* kw = nullptr;               // weighted degrees (integer-weight sweeps)
+  long long cap_kw = 0;
   // float weights in exact fixed point (run on the integer sweeps)
   int f32_fixed = 1;                    // 0: always float64 sums; 1: fixed point when exact
   int* fix_w = nullptr;
@@ -344,6 +346,10 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
   a.btab = c->btab;
   a.btab_region = 2ll * c->ctr_h->max_degree;
   a.n = n;
+  if (weights) {   // weighted degrees, written by sweep 1 for the early stops of later sweeps
+    if (int r = grow(c, c->kw, c->cap_kw, n)) return r;
+    a.kw = c->kw;
+  }
   int t = 0;
   bool converged = false, marked_prev = false;
   long long dn_prev = n;
@@ -855,7 +861,7 @@ int gsl_ctx_destroy(gsl_ctx* c) {
                    c->block_sums, c->partials, c->wtab, c->btab, c->rowbits, c->lg, c->work2, c->fkeys, c->fvals, c->hub_piece_start,
                    c->hub_ustart, c->hub_best, c->hub_own, c->hub_wsum, c->hub_used_cnt, c->hub_clu, c->hub_used, c->hub_tab,
                    c->ctr, c->sums, c->k_dev,
-                   c->st_off, c->st_col, c->st_w, c->st_lab, c->fix_w, c->fix_dev};
+                   c->st_off, c->st_col, c->st_w, c->st_lab, c->fix_w, c->fix_dev, c->kw};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (c->ctr_h) cudaFreeHost(c->ctr_h);

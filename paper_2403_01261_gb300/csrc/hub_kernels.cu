@@ -271,14 +271,15 @@ __device__ __forceinline__ void cluster_row(const SweepArgs& a, int v, int own, 
 }
 
 // The cluster's own-label pass over a hub row (own_weight_pass over the
-// cluster's virtual threads).  With unit weights each warp adds its round's
-// own-label count to rank 0's counter `cnt` and stops once the returned
-// total is more than half of the row's d entries: the own label then holds a
-// strict majority whatever the rest carries.
+// cluster's virtual threads).  Each warp adds its round's own-label weight
+// to rank 0's counter `cnt` and stops once the returned total is more than
+// half of `bound` (the row's d entries, or its weighted degree from sweep
+// 1): the own label then holds a strict majority whatever the rest carries.
 template <bool WEIGHTED, bool ASYNC>
 __device__ __forceinline__ void cluster_own_pass(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
                                                  const int* lp, int d, int tid, int nthr, const Pol& pol,
-                                                 unsigned& own_w, unsigned& tot_w, unsigned* cnt) {
+                                                 unsigned& own_w, unsigned& tot_w, unsigned* cnt,
+                                                 unsigned long long bound) {
   const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
   const int step = nw * 128;
   const int cb = wid * 32 + lane, cu = nw * 32;
@@ -304,15 +305,15 @@ __device__ __forceinline__ void cluster_own_pass(const SweepArgs& a, int v, int 
         tot_w += (unsigned)w[u];
         if (l[u] == own) {
           own_w += (unsigned)w[u];
-          ++o;
+          o += (unsigned)w[u];
         }
       }
     }
-    if (!WEIGHTED && more) {
+    if (more && bound != ~0ull) {
       o = __reduce_add_sync(FULL, o);
       unsigned total = 0;
       if (lane == 0 && o) total = atomicAdd(cnt, o) + o;
-      if (2u * __shfl_sync(FULL, total, 0) > (unsigned)d) return;
+      if (2ull * __shfl_sync(FULL, total, 0) > bound) return;
     }
   }
 }
@@ -377,8 +378,10 @@ __global__ void __launch_bounds__(512, 2) hub_cluster_kernel(SweepArgs a, HubPla
     const int* lp = a.lg ? a.lg + s : nullptr;
     if (maj) {
       unsigned own_w = 0, tot_w = 0;
+      const unsigned long long bound =
+          !WEIGHTED ? (unsigned long long)d : (a.kw ? (unsigned long long)a.kw[v] : ~0ull);
       cluster_own_pass<WEIGHTED, ASYNC>(a, v, own, cp, wp, lp, d, tid, nthr, pol, own_w, tot_w,
-                                        cl.map_shared_rank(&s_mcnt[par], 0));
+                                        cl.map_shared_rank(&s_mcnt[par], 0), bound);
       const unsigned long long ow = warp_sum_u64(own_w), tw = warp_sum_u64(tot_w);
       if ((threadIdx.x & 31) == 0) {
         if (ow) atomicAdd(&s_mown[par], ow);
@@ -393,9 +396,9 @@ __global__ void __launch_bounds__(512, 2) hub_cluster_kernel(SweepArgs a, HubPla
         }
         o = warp_sum_u64(o);
         t = warp_sum_u64(t);
-        // a strict majority of the row, or (unit weights, the pass stopped
-        // early) more than half of its d entries
-        if (threadIdx.x == 0) s_skip[par] = 2 * o > t || (!WEIGHTED && 2 * o > (unsigned long long)d);
+        // a strict majority of the row, or (the pass stopped early) more
+        // than half of its total
+        if (threadIdx.x == 0) s_skip[par] = 2 * o > t || 2 * o > bound;
       }
       __syncthreads();
       if (s_skip[par]) continue;   // the label stays (hp.best 0, hp.own 0)
@@ -502,6 +505,7 @@ __global__ void __launch_bounds__(256) hub_final_kernel(SweepArgs a, HubPlan hp,
     const bool changed = nl != old;
     if (threadIdx.x == 0) {
       if (weighted && a.check && hp.wsum[i] >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+      if (weighted && a.check && a.kw) a.kw[v] = hp.wsum[i] < (1ull << 32) ? (unsigned)hp.wsum[i] : ~0u;
       store_label<ASYNC>(a, v, nl, changed);
       if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;

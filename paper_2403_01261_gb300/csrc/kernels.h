@@ -32,6 +32,8 @@ struct SweepArgs {
   int mark;                  // mark neighbours of changed vertices in fnext
   const int* lg;             // sync mode: labels gathered per entry, lg[e] = prev[col[e]] (null: gather)
   int spread;                // labels read are nearly all distinct (sweep 2 from the identity labelling)
+  unsigned* kw;              // weighted degree per vertex of classes 6-9: written in sweep 1 (check), then read by
+                             // the early stops of the majority filter and the hub clusters (null: none)
 };
 
 struct Tuning {

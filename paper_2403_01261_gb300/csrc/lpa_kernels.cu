@@ -306,9 +306,11 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
       // of the row is not needed (after sweep 1, which reads every entry)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const bool mine = l[u] == own;
-        own_sum += (unsigned)__popc(__ballot_sync(FULL, mine));
-        if (mine) l[u] = -1;
+        if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
+          const bool mine = l[u] == own;
+          own_sum += (unsigned)__popc(__ballot_sync(FULL, mine));
+          if (mine) l[u] = -1;
+        }
       }
       if (!a.check && 2u * own_sum > (unsigned)d) return false;
     }
@@ -406,6 +408,7 @@ __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(Swee
     if (WEIGHTED && a.check) {
       wsum = warp_sum_u64(wsum);
       if (lane == 0 && wsum >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+      if (lane == 0 && a.kw) a.kw[v] = wsum < (1ull << 32) ? (unsigned)wsum : ~0u;
     }
     const int nl = best ? (int)~(unsigned)best : old;
     const bool changed = nl != old;
@@ -506,6 +509,7 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
     const bool changed = nl != old;
     if (threadIdx.x == 0) {
       if (WEIGHTED && a.check && sh.wsum[par] >= (1ull << 31)) raise_err(&a.ctr->err, ERRBIT_OVERFLOW);
+      if (WEIGHTED && a.check && a.kw) a.kw[v] = sh.wsum[par] < (1ull << 32) ? (unsigned)sh.wsum[par] : ~0u;
       store_label<ASYNC>(a, v, nl, changed);
       if (changed) count_graph_change(a, v);
       my_scan += (unsigned long long)d;
@@ -529,15 +533,16 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
 
 // ---------------------------------------------------------------------------
 // The filter's pass over one row, one warp (own_weight_pass with 32
-// threads): with unit weights it stops as soon as the own label holds more
-// than half of the row's d entries, since it then holds a strict majority
-// of the whole row whatever the rest carries (`early`).  Returns the
-// entries read.
+// threads): it stops as soon as the own label holds more than half of the
+// row's total (d entries, or the weighted degree from sweep 1), since it
+// then holds a strict majority of the whole row whatever the rest carries
+// (`early`).  Returns the entries read.
 template <bool WEIGHTED, bool ASYNC>
 __device__ __forceinline__ int filter_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
                                           const int* lp, int d, const Pol& pol, unsigned& own_w, unsigned& tot_w,
                                           bool& early) {
   const int lane = threadIdx.x & 31;
+  const unsigned long long bound = !WEIGHTED ? (unsigned long long)d : (a.kw ? (unsigned long long)a.kw[v] : ~0ull);
   int jn[4], wn[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, lane + 32 * u, pol, jn[u], wn[u]);
@@ -560,7 +565,7 @@ __device__ __forceinline__ int filter_row(const SweepArgs& a, int v, int own, co
         if (l[u] == own) own_w += (unsigned)w[u];
       }
     }
-    if (!WEIGHTED && more && 2u * __reduce_add_sync(FULL, own_w) > (unsigned)d) {
+    if (more && 2ull * __reduce_add_sync(FULL, own_w) > bound) {
       early = true;
       return r0 + 128;
     }
