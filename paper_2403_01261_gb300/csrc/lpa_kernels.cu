@@ -715,11 +715,16 @@ __device__ __forceinline__ long long row_of(const long long* off, long long n, l
 
 // Entry e (column je) against entry e + 1 (column jn): the row is not
 // strictly increasing if e + 1 continues e's row and jn <= je.
+__device__ __forceinline__ void check_order(const long long* off, long long n, long long nnz, const unsigned* bits,
+                                            unsigned char* bad, long long e, int je, int jn) {
+  const long long f = e + 1;
+  if (f < nnz && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0 && !(je < jn)) bad[row_of(off, n, e)] = 1;
+}
+
 __device__ __forceinline__ void check_pair(const long long* off, long long n, long long nnz, const unsigned* bits,
                                            unsigned char* bad, Counters* ctr, long long e, int je, int jn) {
   if ((unsigned)je >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
-  const long long f = e + 1;
-  if (f < nnz && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0 && !(je < jn)) bad[row_of(off, n, e)] = 1;
+  check_order(off, n, nnz, bits, bad, e, je, jn);
 }
 
 // Sixteen entries per thread per round, as four 16-byte loads issued
@@ -763,10 +768,16 @@ __global__ void __launch_bounds__(256) sorted_check_kernel(const long long* __re
       if (q < nq) {
         const long long e = head + 4 * q;
         if (q + 1 >= nq) nx = e + 4 < nnz ? col[e + 4] : 0;   // the next entry lies in the scalar tail
-        check_pair(off, n, nnz, bits, bad, ctr, e, v[u].x, v[u].y);
-        check_pair(off, n, nnz, bits, bad, ctr, e + 1, v[u].y, v[u].z);
-        check_pair(off, n, nnz, bits, bad, ctr, e + 2, v[u].z, v[u].w);
-        check_pair(off, n, nnz, bits, bad, ctr, e + 3, v[u].w, nx);
+        const unsigned mx = max(max((unsigned)v[u].x, (unsigned)v[u].y), max((unsigned)v[u].z, (unsigned)v[u].w));
+        if (mx >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
+        // four increasing pairs need no row bounds: only a quad with a
+        // descent (a row start, or a row out of order) is checked pair by pair
+        if (!(v[u].x < v[u].y && v[u].y < v[u].z && v[u].z < v[u].w && (v[u].w < nx || e + 4 >= nnz))) {
+          check_order(off, n, nnz, bits, bad, e, v[u].x, v[u].y);
+          check_order(off, n, nnz, bits, bad, e + 1, v[u].y, v[u].z);
+          check_order(off, n, nnz, bits, bad, e + 2, v[u].z, v[u].w);
+          check_order(off, n, nnz, bits, bad, e + 3, v[u].w, nx);
+        }
       }
     }
   }
