@@ -109,7 +109,12 @@ __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ 
         if (act && gid && done[gid[v]]) act = false;   // batched: this vertex's graph has stopped
         if (act) cls[k] = degree_class(off[v + 1] - off[v], cb.warp_small, cb.warp_max, cb.blk_max);
       }
-      if (cls[k] >= 0) pos[k] = atomicAdd(&cnt[cls[k]], 1u);
+      // one shared-memory add per class present in the warp
+      const unsigned m = __match_any_sync(FULL, cls[k]);
+      const int leader = __ffs(m) - 1;
+      unsigned b = 0;
+      if ((int)(threadIdx.x & 31) == leader && cls[k] >= 0) b = atomicAdd(&cnt[cls[k]], (unsigned)__popc(m));
+      pos[k] = __shfl_sync(FULL, b, leader) + (unsigned)__popc(m & lanemask_lt());
     }
     __syncthreads();
     if (threadIdx.x < NCLASS) base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&ctr->cls_count[threadIdx.x], cnt[threadIdx.x]) : 0u;
