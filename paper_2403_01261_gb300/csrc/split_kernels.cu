@@ -97,13 +97,30 @@ __global__ void init_parent_kernel(int* __restrict__ p, long long n) {
 
 // Phase 1: every vertex links with the first SPLIT_SAMPLE same-community
 // neighbours among its first SPLIT_SCAN row entries.
+// The first two entries' columns and labels are requested together; the
+// rest of the scan (when they are not both links) goes one entry at a time.
 __global__ void sample_link_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                    const int* __restrict__ labels, int* p, long long n, Counters* ctr) {
+  static_assert(SPLIT_SAMPLE == 2, "the first two entries are loaded together");
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
     const long long s = off[u], e = off[u + 1];
+    if (s >= e) continue;
     const int cu = labels[u];
+    const int j0 = ld_stream(col + s), j1 = s + 1 < e ? ld_stream(col + s + 1) : -1;
+    const bool v0 = (unsigned)j0 < (unsigned)n, v1 = (unsigned)j1 < (unsigned)n;
+    if (!v0 || (s + 1 < e && !v1)) raise_err(&ctr->err, ERRBIT_INVALID);
+    const int l0 = v0 && j0 != (int)u ? ld_label_ro(labels + j0) : ~cu;
+    const int l1 = v1 && j1 != (int)u ? ld_label_ro(labels + j1) : ~cu;
     int linked = 0;
-    for (int k = 0; k < SPLIT_SCAN && linked < SPLIT_SAMPLE && s + k < e; ++k)
+    if (l0 == cu) {
+      uf_unite(p, (int)u, j0, &ctr->err);
+      ++linked;
+    }
+    if (l1 == cu) {
+      uf_unite(p, (int)u, j1, &ctr->err);
+      ++linked;
+    }
+    for (int k = 2; k < SPLIT_SCAN && linked < SPLIT_SAMPLE && s + k < e; ++k)
       linked += hook_entry(col, labels, p, n, (int)u, cu, s + k, &ctr->err) ? 1 : 0;
   }
 }
