@@ -1,25 +1,29 @@
-// hub_kernels.cu -- the sweep for hub vertices (class 9), split into pieces.
+// hub_kernels.cu -- the sweep for hub vertices (class 9).
 //
 // One block per hub would leave the largest rows (a million entries and
-// more on R-MAT scale 25) to a single SM at the end of the launch.  Here a
-// hub's row is cut into pieces of HUB_PIECE entries, and any block may take
-// any piece:
-//   1. hub_plan_kernel (one block): numbers the pieces of the frontier's
-//      hubs (prefix sums) and places every hub's global table region
-//      (2 d slots) and used-slot list (d entries);
-//   2. hub_piece_kernel: a block aggregates one piece in a shared-memory
-//      table (a piece has at most HUB_PIECE < 3/4 of the table's slots
-//      distinct labels, so it never overflows), then adds each of its
-//      (label, sum) pairs to the hub's global table.  Every add returns the
-//      label's new total, so the largest packed key (sum << 32 | ~label)
-//      over all adds of all pieces is the hub's argmax with smallest-label
-//      ties -- the same argument as within one block; it is combined with
-//      one atomicMax per piece.  Entries carrying the hub's own label are
-//      counted separately and added once per piece;
+// more on R-MAT scale 25) to a single SM at the end of the launch.  Two
+// designs share the plan and final kernels:
+//   1. hub_plan_kernel (one block): lists the frontier's hubs up to the
+//      cluster bound for the cluster kernel (the longest first), numbers the
+//      pieces of the others (prefix sums), and places every hub's global
+//      table region (2 d slots) and used-slot list (d entries);
+//   2a. hub_cluster_kernel (default, every hub): one 8-CTA thread-block
+//      cluster per row, the row's label table spread over the CTAs' shared
+//      memories and filled with distributed-shared-memory atomics; each CTA
+//      then scans its own table for the largest packed key (see the kernel);
+//   2b. hub_piece_kernel: a block aggregates one 8192-entry piece in a
+//      shared-memory table (a piece has at most HUB_PIECE < 3/4 of the
+//      table's slots distinct labels, so it never overflows), then adds each
+//      of its (label, sum) pairs to the hub's global table.  Every add
+//      returns the label's new total, so the largest packed key
+//      (sum << 32 | ~label) over all adds of all pieces is the hub's argmax
+//      with smallest-label ties -- the same argument as within one block; it
+//      is combined with one atomicMax per piece.  Entries carrying the hub's
+//      own label are counted separately and added once per piece;
 //   3. hub_final_kernel: per hub, the own-label key is compared with the
 //      best key, the label written and counted, the table slots the pieces
-//      claimed are reset (the tables stay empty between sweeps), and the
-//      neighbours of a changed hub are marked.
+//      (or an overflowed cluster) claimed are reset (the tables stay empty
+//      between sweeps), and the neighbours of a changed hub are marked.
 #include <cooperative_groups.h>
 
 #include "sweep_device.cuh"
