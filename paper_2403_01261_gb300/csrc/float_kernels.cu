@@ -496,11 +496,7 @@ cudaError_t launch_f_t(const SweepArgs& a, const float* wf, int cls, unsigned* g
     default: {
       const unsigned tb = F_TABLE_SLOTS;
       const size_t smem = (size_t)tb * (sizeof(double) + sizeof(unsigned));
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(sweep_f_block_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-      }
+      raise_smem_limit((const void*)sweep_f_block_kernel<A>, smem);
       sweep_f_block_kernel<A><<<F_BLOCKS_PER_SM * di.sm_count, F_BLOCK, smem, s>>>(a, wf, cls, tb, gkeys, gvals,
                                                                                    region);
     }

@@ -536,13 +536,12 @@ namespace {
 // (0: such clusters cannot run); cached per size.
 template <bool W, bool A>
 int cluster_slots(size_t smem) {
-  static size_t cached_smem = 0;
-  static int cached = 0;
+  thread_local size_t cached_smem = 0;   // per host thread (see block_grid_size)
+  thread_local int cached = 0;
   if (cached_smem == smem) return cached;
   cached_smem = smem;
   cached = 0;
-  if (cudaFuncSetAttribute(hub_cluster_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess ||
+  if (raise_smem_limit((const void*)hub_cluster_kernel<W, A>, smem) != cudaSuccess ||
       (HUB_CLUSTER > 8 &&
        cudaFuncSetAttribute(hub_cluster_kernel<W, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
            cudaSuccess)) {
@@ -573,11 +572,7 @@ template <bool W, bool A>
 cudaError_t launch_hub_t(const SweepArgs& a, const HubPlan& hp, bool maj, const Tuning& t, const DeviceInfo& di,
                          cudaStream_t s, int* kernels) {
   const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
-  static size_t attr_smem = 0;
-  if (attr_smem != smem) {
-    cudaFuncSetAttribute(hub_piece_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_smem = smem;
-  }
+  raise_smem_limit((const void*)hub_piece_kernel<W, A>, smem);
   const int nclusters = t.hub_cluster_max > 0 ? cluster_slots<W, A>(smem) : 0;
   hub_plan_kernel<<<1, 1024, 0, s>>>(a, hp, nclusters > 0 ? (long long)t.hub_cluster_max : 0ll);
   int launches = 3;

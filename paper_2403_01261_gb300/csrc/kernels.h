@@ -72,6 +72,10 @@ cudaError_t launch_sweep(const SweepArgs& a, bool weighted, bool async_mode, con
 cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool async_mode, const Tuning& t,
                                const DeviceInfo& di, cudaStream_t s);
 void count_launches(long long k);   // process-wide tally of kernels this library launched
+// Raises kernel fn's dynamic shared-memory limit to at least `bytes` (never
+// lowers it, so launches of other host threads with smaller tables stay
+// valid); thread-safe.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 long long launches_total();
 // Own-label majority filter over classes 7 and 8: settled rows keep their
 // label; the others go to `out` (n ints, class regions as in the worklist)

@@ -29,6 +29,8 @@
 // labels only, so skipping the other vertices gives the same labels as a
 // full sweep.
 #include <atomic>
+#include <mutex>
+#include <unordered_map>
 
 #include "sweep_device.cuh"
 
@@ -854,7 +856,7 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
   switch (cls) {
 #define GSL_LAUNCH_GROUP(G, CLS)                                                                 \
   case CLS: {                                                                                    \
-    static int grid = 0;                                                                         \
+    thread_local int grid = 0;                                                                   \
     if (!grid) grid = occupancy_grid(sweep_group_kernel<G, W, A>, t.group_block, 0, di);         \
     sweep_group_kernel<G, W, A><<<grid, t.group_block, 0, s>>>(a, CLS);                          \
     break;                                                                                       \
@@ -868,10 +870,9 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
 #undef GSL_LAUNCH_GROUP
     case CLS_WARP_S: {
       const size_t smem = (size_t)(t.warp_block / 32) * TW_SMALL * sizeof(unsigned long long);
-      static int grid = 0;
+      thread_local int grid = 0;
       if (!grid) {
-        cudaFuncSetAttribute(sweep_warp_kernel<W, A, TW_SMALL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        raise_smem_limit((const void*)sweep_warp_kernel<W, A, TW_SMALL, false>, smem);
         grid = occupancy_grid(sweep_warp_kernel<W, A, TW_SMALL, false>, t.warp_block, smem, di);
       }
       sweep_warp_kernel<W, A, TW_SMALL, false><<<grid, t.warp_block, smem, s>>>(a, CLS_WARP_S);
@@ -879,10 +880,9 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
     }
     case CLS_WARP_L: {
       const size_t smem = (size_t)(t.warp_block / 32) * TW_LARGE * sizeof(unsigned long long);
-      static int grid = 0;
+      thread_local int grid = 0;
       if (!grid) {
-        cudaFuncSetAttribute(sweep_warp_kernel<W, A, TW_LARGE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        raise_smem_limit((const void*)sweep_warp_kernel<W, A, TW_LARGE, true>, smem);
         grid = occupancy_grid(sweep_warp_kernel<W, A, TW_LARGE, true>, t.warp_block, smem, di);
       }
       sweep_warp_kernel<W, A, TW_LARGE, true><<<grid, t.warp_block, smem, s>>>(a, CLS_WARP_L);
@@ -891,11 +891,7 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
     case CLS_BLOCK:
     case CLS_HUB: {
       const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
-      static size_t attr_smem = 0;
-      if (attr_smem != smem) {
-        cudaFuncSetAttribute(sweep_block_kernel<W, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_smem = smem;
-      }
+      raise_smem_limit((const void*)sweep_block_kernel<W, A>, smem);
       const int grid = (int)block_grid_size(t, di);
       sweep_block_kernel<W, A><<<grid, t.blk_block, smem, s>>>(a, cls, (unsigned)t.blk_slots,
                                                                cls == CLS_HUB ? a.gthresh : 0);
@@ -910,15 +906,27 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
 }  // namespace
 
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> limits;
+  std::lock_guard<std::mutex> g(mu);
+  size_t& cur = limits[fn];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 long long block_grid_size(const Tuning& t, const DeviceInfo& di) {
-  static long long cached = 0;
-  static int cached_slots = 0, cached_block = 0;
+  // per host thread: contexts with different block shapes may run on several threads at once
+  thread_local long long cached = 0;
+  thread_local int cached_slots = 0, cached_block = 0;
   if (cached && cached_slots == t.blk_slots && cached_block == t.blk_block) return cached;
   int per_sm = 0;
   const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
-  cudaFuncSetAttribute(sweep_block_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void*)sweep_block_kernel<false, false>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_block_kernel<false, false>, t.blk_block, smem);
   cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
@@ -931,8 +939,7 @@ long long block_grid_size(const Tuning& t, const DeviceInfo& di) {
 long long warp_grid_warps(const Tuning& t, const DeviceInfo& di) {
   int per_sm = 0;
   const size_t smem = (size_t)(t.warp_block / 32) * TW_LARGE * sizeof(unsigned long long);
-  cudaFuncSetAttribute(sweep_warp_kernel<false, false, TW_LARGE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
+  raise_smem_limit((const void*)sweep_warp_kernel<false, false, TW_LARGE, true>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_warp_kernel<false, false, TW_LARGE, true>,
                                                 t.warp_block, smem);
   cudaGetLastError();
