@@ -477,6 +477,67 @@ __global__ void __launch_bounds__(256) mod_f_square_kernel(const double* __restr
   if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(sums + 2, acc);
 }
 
+// Own-label majority filter with float weights for classes 7 and 8, as the
+// integer filter (lpa_kernels.cu): one warp per row sums, in float64, the
+// weights of the entries carrying the vertex's own label and of all entries
+// (the vertex itself excluded); a strict majority keeps the label (Eq. 2's
+// argmax), other rows go to `out` for the table kernel.  Four 32-entry
+// chunks are loaded before they are summed.
+template <bool ASYNC>
+__global__ void __launch_bounds__(256) majority_filter_f_kernel(SweepArgs a, const float* __restrict__ wf,
+                                                                int* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const Pol pol = make_pol();
+  const long long c7 = a.ctr->cls_count[CLS_WARP_L];
+  const long long total = c7 + a.ctr->cls_count[CLS_BLOCK];
+  unsigned long long my_scan = 0, my_settled = 0;
+  for (long long i = warp; i < total; i += nwarps) {
+    const int cls = i < c7 ? CLS_WARP_L : CLS_BLOCK;
+    const long long start = a.ctr->cls_start[cls];
+    const int v = a.work[start + (i < c7 ? i : i - c7)];
+    const long long s = a.off[v];
+    const int d = (int)(a.off[v + 1] - s);
+    const int old = own_label<ASYNC>(a, v);
+    double ow = 0.0, tw = 0.0;
+    for (int e0 = 0; e0 < d; e0 += 128) {
+      int j[4];
+      float w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_entry_f(a, a.col + s, wf + s, d, e0 + 32 * u + lane, pol, j[u], w[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int l = entry_label<ASYNC>(a, nullptr, e0 + 32 * u + lane, j[u], v, pol);
+        if (l >= 0) {
+          tw += (double)w[u];
+          if (l == old) ow += (double)w[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      ow += __shfl_xor_sync(FULL, ow, o);
+      tw += __shfl_xor_sync(FULL, tw, o);
+    }
+    if (lane == 0) {
+      if (2.0 * ow > tw) {
+        store_label<ASYNC>(a, v, old, false);
+        my_scan += (unsigned long long)d;
+        my_settled += 1;
+      } else {
+        out[start + atomicAdd(&a.ctr->uns_count[cls], 1u)] = v;
+      }
+    }
+  }
+  my_scan = warp_sum_u64(my_scan);
+  my_settled = warp_sum_u64(my_settled);
+  if (lane == 0) {
+    if (my_scan) atomicAdd(&a.ctr->scanned, my_scan);
+    if (my_settled) atomicAdd(&a.ctr->fast_active, my_settled);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 namespace {
 template <bool A>
@@ -507,6 +568,16 @@ cudaError_t launch_f_t(const SweepArgs& a, const float* wf, int cls, unsigned* g
 }  // namespace
 
 long long float_table_blocks(const DeviceInfo& di) { return (long long)F_BLOCKS_PER_SM * di.sm_count; }
+
+cudaError_t launch_majority_filter_f32(const SweepArgs& a, const float* wf, int* out, bool async_mode,
+                                       const DeviceInfo& di, cudaStream_t s) {
+  const int grid = 16 * di.sm_count;
+  if (async_mode) majority_filter_f_kernel<true><<<grid, 256, 0, s>>>(a, wf, out);
+  else majority_filter_f_kernel<false><<<grid, 256, 0, s>>>(a, wf, out);
+  count_launches(1);
+  if (cudaError_t e = cudaGetLastError()) return e;
+  return launch_filter_counts(a.ctr, a.stop, s);
+}
 
 cudaError_t launch_sweep_f32(const SweepArgs& a, const float* wf, int cls, bool async_mode, unsigned* gkeys,
                              double* gvals, long long region, const DeviceInfo& di, cudaStream_t s) {

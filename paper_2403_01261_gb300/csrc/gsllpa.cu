@@ -561,9 +561,20 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
     a.fnext = c->flag[(t + 1) & 1];
     a.check = t == 1 ? 1 : 0;
     a.mark = (t > 1 && 2 * dn_prev <= n) ? 1 : 0;
+    // the own-label majority filter for classes 7 and 8, as in run_lpa
+    const bool filter = !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
+    SweepArgs af = a;
+    if (filter) {
+      if (int r = grow(c, c->work2, c->cap_work2, n)) return r;
+      const int pe = prof_begin(c, s);
+      CK(launch_majority_filter_f32(a, wf, c->work2, async_mode, c->di, s));
+      prof_end(c, pe, SL_FILTER, s, 2);
+      af.work = c->work2;
+    }
     for (int k = 0; k < NCLASS; ++k) {
       const int pe = prof_begin(c, s);
-      CK(launch_sweep_f32(a, wf, k, async_mode, c->fkeys, c->fvals, region, c->di, s));
+      CK(launch_sweep_f32(k == CLS_WARP_L || k == CLS_BLOCK ? af : a, wf, k, async_mode, c->fkeys, c->fvals, region,
+                          c->di, s));
       prof_end(c, pe, SL_SWEEP0 + k, s, 1);
     }
     CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
@@ -582,6 +593,19 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
         sl.entries += e;
         sl.bytes += 20.0 * (double)v + 12.0 * (double)e;
         act_all += v;
+      }
+      if (filter) {   // the filter read every row of classes 7 and 8 (as in run_lpa)
+        long long cls_e = 0, rows = (long long)c->ctr_h->fast_active;
+        for (int k = 0; k < NCLASS; ++k) cls_e += (long long)c->ctr_h->cls_scanned[k];
+        long long fe = (long long)c->ctr_h->scanned - cls_e;
+        for (int k = CLS_WARP_L; k <= CLS_BLOCK; ++k) {
+          fe += (long long)c->ctr_h->cls_scanned[k];
+          rows += c->ctr_h->cls_count[k];
+        }
+        auto& sf = c->profile.slot[SL_FILTER];
+        sf.vertices += rows;
+        sf.entries += fe;
+        sf.bytes += 20.0 * (double)rows + 12.0 * (double)fe;
       }
       auto& sb = c->profile.slot[SL_BIN];
       sb.vertices += all_active ? n : act_all;

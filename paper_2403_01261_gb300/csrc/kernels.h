@@ -81,6 +81,8 @@ long long launches_total();
 // label; the others go to `out` (n ints, class regions as in the worklist)
 // and become the class counts of the table kernels, which must then read
 // `out` as their worklist.
+// The class counts of classes 7-8 become the rows a filter passed on.
+cudaError_t launch_filter_counts(Counters* ctr, const int* stop, cudaStream_t s);
 cudaError_t launch_majority_filter(const SweepArgs& a, int* out, bool weighted, bool async_mode,
                                    const DeviceInfo& di, cudaStream_t s);
 // Edge-parallel label gather for a synchronous sweep: lg[e] = prev[col[e]]
@@ -147,6 +149,10 @@ cudaError_t launch_hub_pieces(const SweepArgs& a, const HubPlan& hp, bool weight
 long long float_table_blocks(const DeviceInfo& di);
 cudaError_t launch_sweep_f32(const SweepArgs& a, const float* wf, int cls, bool async_mode, unsigned* gkeys,
                              double* gvals, long long region, const DeviceInfo& di, cudaStream_t s);
+// Own-label majority filter for float weights (classes 7-8, float64 sums),
+// as launch_majority_filter.
+cudaError_t launch_majority_filter_f32(const SweepArgs& a, const float* wf, int* out, bool async_mode,
+                                       const DeviceInfo& di, cudaStream_t s);
 // Exact fixed-point form of float weights (float_kernels.cu): out[0..2] =
 // 1024 + lowest set-bit exponent, 1024 + highest set-bit exponent, invalid
 // flag; then wi[e] = w[e] * 2^shift.

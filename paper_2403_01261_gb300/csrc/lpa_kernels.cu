@@ -639,6 +639,12 @@ __global__ void filter_counts_kernel(Counters* ctr, const int* stop) {
   for (int k = CLS_WARP_L; k <= CLS_BLOCK; ++k) ctr->cls_count[k] = ctr->uns_count[k];
 }
 
+cudaError_t launch_filter_counts(Counters* ctr, const int* stop, cudaStream_t s) {
+  filter_counts_kernel<<<1, 1, 0, s>>>(ctr, stop);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_majority_filter(const SweepArgs& a, int* out, bool weighted, bool async_mode,
                                    const DeviceInfo& di, cudaStream_t s) {
   const int grid = 16 * di.sm_count;
