@@ -424,7 +424,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
       prof_end(c, pe, SL_FILTER, s, 2);
       af.work = c->work2;
     }
-    for (int k = 0; k < NCLASS; ++k) {
+    for (int k = NCLASS - 1; k >= 0; --k) {   // the longest rows first
       const int pe = prof_begin(c, s);
       if (k == CLS_WARP_L || k == CLS_BLOCK) {
         CK(launch_sweep_class(af, k, weights != nullptr, async_mode, c->tune, c->di, s));
