@@ -475,6 +475,28 @@ def test_float_lpa_with_integer_weights_equals_integer_lpa():
         assert O.modularity_f64(g, wi.astype(np.float32), lab_i) == pytest.approx(O.modularity(h, lab_i), abs=1e-12)
 
 
+def test_float_lpa_with_dyadic_weights_equals_integer_lpa_on_scaled_weights():
+    """Weights that are multiples of 2^-S with small row totals: every float64
+    partial sum is exact, so the float oracle's labels equal the integer
+    oracle's on the weights times 2^S (the form the library runs such
+    weights in).  S = 3 (k/8) and S = 20 (1 + k/2^20)."""
+    rng = np.random.default_rng(5)
+    for g in (I.sbm_planted(3000, 60, 10.0, 2.0, seed=6), I.rmat(11, 8, seed=4)):
+        src = np.repeat(np.arange(g.n), np.diff(g.offsets))
+        key = np.minimum(src, g.cols).astype(np.int64) * g.n + np.maximum(src, g.cols)
+        uniq, inv = np.unique(key, return_inverse=True)
+        for shift, vals in ((3, rng.integers(1, 33, uniq.shape[0]) / 8.0),
+                            (20, 1.0 + rng.integers(0, 1 << 20, uniq.shape[0]) / float(1 << 20))):
+            wf = vals[inv].astype(np.float32)
+            wi = (wf.astype(np.float64) * (1 << shift)).astype(np.int64)
+            assert np.array_equal(wi.astype(np.float64), wf.astype(np.float64) * (1 << shift))
+            assert wi.max() < (1 << 31)
+            gi = I.Graph(g.offsets, g.cols, wi.astype(np.int32), name=g.name + "-scaled")
+            lf, tf, dnf = O.lpa_sync_f32(g, wf, 0.05, 20)
+            li, ti, dni = O.lpa_sync(gi, 0.05, 20)
+            assert tf == ti and np.array_equal(dnf, dni) and np.array_equal(lf, li), (g.name, shift)
+
+
 def test_float_modularity_matches_networkx():
     nx = pytest.importorskip("networkx")
     rng = np.random.default_rng(43)
