@@ -497,6 +497,34 @@ def test_float_lpa_with_dyadic_weights_equals_integer_lpa_on_scaled_weights():
             assert tf == ti and np.array_equal(dnf, dni) and np.array_equal(lf, li), (g.name, shift)
 
 
+def test_own_label_majority_keeps_the_label():
+    """The own-label majority shortcut: a vertex whose own label holds more
+    than half of its row's weight (the vertex itself excluded) keeps it in
+    a synchronous sweep; so does one whose own label holds more than half of
+    an upper bound of that weight -- its entry count d with unit weights, or
+    its weighted degree including self-loops.  Checked on random labellings
+    concentrated enough that many vertices qualify."""
+    rng = np.random.default_rng(12)
+    base = I.rmat(10, 12, seed=7)
+    for w in (False, True):
+        wi = I.symmetric_weights(base, 3, 9) if w else np.ones(base.nnz, np.int32)
+        g = I.Graph(base.offsets, base.cols, wi if w else None)
+        src = np.repeat(np.arange(g.n), np.diff(g.offsets))
+        checked = 0
+        for trial in range(6):
+            prev = rng.integers(0, 3 + trial, g.n).astype(np.int32)
+            nxt, _ = O.sync_sweep(g, prev)
+            same = prev[g.cols] == prev[src]
+            notself = g.cols != src
+            own = np.bincount(src, weights=wi * (same & notself), minlength=g.n)
+            tot = np.bincount(src, weights=wi * notself, minlength=g.n)
+            bound = np.bincount(src, weights=wi, minlength=g.n)   # includes self-loop entries
+            for cond in (2 * own > tot, 2 * own > bound):
+                assert np.array_equal(nxt[cond], prev[cond])
+                checked += int(cond.sum())
+        assert checked > 100
+
+
 def test_float_modularity_matches_networkx():
     nx = pytest.importorskip("networkx")
     rng = np.random.default_rng(43)
