@@ -525,6 +525,34 @@ def test_own_label_majority_keeps_the_label():
         assert checked > 100
 
 
+def test_first_sweep_of_increasing_rows_takes_the_first_other_entry():
+    """Reading 12: from the identity labels with unit weights, a strictly
+    increasing row holds every label once, so Eq. 2's tie rule picks its
+    smallest neighbour other than the vertex: the first entry, or the second
+    when the first is a self-loop."""
+    g0 = I.rmat(11, 8, seed=8)
+    # add self-loops to a few rows, keeping them strictly increasing
+    rng = np.random.default_rng(8)
+    pick = set(rng.choice(g0.n, 40, replace=False).tolist())
+    rows = []
+    for v in range(g0.n):
+        r = g0.cols[g0.offsets[v]:g0.offsets[v + 1]]
+        if v in pick:
+            r = np.unique(np.append(r, v))
+        rows.append(r.astype(np.int32))
+    off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    g = I.Graph(off, np.concatenate(rows))
+    got, _ = O.sync_sweep(g, np.arange(g.n, dtype=np.int32))
+    want = np.arange(g.n, dtype=np.int32)
+    for v in range(g.n):
+        r = g.cols[g.offsets[v]:g.offsets[v + 1]]
+        assert (np.diff(r) > 0).all()
+        r = r[r != v]
+        if r.size:
+            want[v] = r[0]
+    assert np.array_equal(got, want)
+
+
 def test_float_modularity_matches_networkx():
     nx = pytest.importorskip("networkx")
     rng = np.random.default_rng(43)
