@@ -1,7 +1,7 @@
 """CPU oracle for GSL-LPA (test infrastructure only).
 
 Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
-baseline may import this package.  It wraps ``oracle.c`` (plain, single
+baseline and reference arm may import this package.  It wraps ``oracle.c`` (plain, single
 threaded C that shares nothing with the CUDA library) with numpy in and out.
 
 Functions and the passages they follow:

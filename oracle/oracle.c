@@ -2,10 +2,10 @@
  * oracle.c -- plain single-threaded CPU oracle for GSL-LPA.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
- * benchmark's CPU-baseline leg may load this file.  It shares no code, header
- * or table with the CUDA library and is written for a reader checking it
- * against the paper line by line: dense arrays, plain loops, no pruning where
- * pruning is not part of the definition, exact integer sums.
+ * benchmark's CPU-baseline and reference legs may load this file.  It shares
+ * no code, header or table with the CUDA library and is written for a reader
+ * checking it against the paper step by step: dense arrays, plain loops, no
+ * pruning where pruning is not part of the definition, exact integer sums.
  *
  * Graph: symmetric CSR, int64 offsets[n+1], int32 cols[nnz], optional int32
  * weights[nnz] (NULL means every edge weighs 1), as in Section 3 ("unweighted
