@@ -84,12 +84,13 @@ int gsl_ctx_destroy(gsl_ctx* ctx);
 
 /* Degree-class thresholds of the sweep kernels: vertices of degree
  * 33..warp_max are handled by one warp each, degree warp_max+1..blk_max by
- * one block each, larger degrees (hubs) by one block each that may go
- * straight to global-memory tables.  Label sums use shared-memory hash
- * tables (8 KB per warp, 96 KB per block) and spill to context-owned
- * global tables when a vertex has more distinct neighbour labels than fit.
- * Defaults 1024 and 32768.  Requires 32 <= warp_max <= 2^20 and
- * warp_max <= blk_max.  Results do not depend on these values. */
+ * one block each, larger degrees (hubs) by one 8-CTA thread-block cluster
+ * each (or in 8192-entry pieces spread over blocks: see
+ * gsl_ctx_set_hub_cluster).  Label sums use shared-memory hash tables
+ * (8 KB per warp, 96 KB per block, 8 x 96 KB per cluster) and spill to
+ * context-owned global tables when a vertex has more distinct neighbour
+ * labels than fit.  Defaults 1024 and 32768.  Requires 32 <= warp_max <=
+ * 2^20 and warp_max <= blk_max.  Results do not depend on these values. */
 int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
 
 /* Shape of the block kernel (degree warp_max+1..blk_max and hub pieces):
@@ -140,31 +141,62 @@ int gsl_ctx_set_f32_fixed(gsl_ctx* ctx, int32_t mode);
  * < 0: GSL_ERR_INVALID.  Labels and statistics do not depend on it. */
 int gsl_ctx_set_hub_cluster(gsl_ctx* ctx, int64_t max_degree);
 
-/* Result of gsl_autotune. */
+/* Bounds of the device-side retry loops (the paper has no counterpart).
+ * Every open-addressing insert of the sweep tables stops after probe_bound
+ * probes, and every union-find find or union of the split after
+ * unionfind_bound steps; a loop that reaches its bound raises an error bit,
+ * the kernel finishes without waiting on anything, and the call returns
+ * GSL_ERR_TIMEOUT (labels unspecified).  The defaults (2^24 probes, 2^26
+ * steps) cannot be reached on valid input: tables always keep free slots
+ * and union-find paths are shorter than n.  Lower values exist so that
+ * tests can drive that error path without a fault or a hang.  0 restores a
+ * default; negative values: GSL_ERR_INVALID. */
+int gsl_ctx_set_retry_bounds(gsl_ctx* ctx, int32_t probe_bound, int32_t unionfind_bound);
+
+/* Result of gsl_autotune and gsl_autotune_batch: the chosen setting (now
+ * set on the context) and the timings. */
 typedef struct {
-  int32_t warp_max;     /* chosen thresholds (now set on the context) */
+  int32_t warp_max;     /* degree-class thresholds (gsl_ctx_set_tuning) */
   int32_t blk_max;
-  int32_t pregather;    /* chosen two-phase mode (gsl_ctx_set_pregather) */
+  int32_t pregather;    /* two-phase mode (gsl_ctx_set_pregather) */
   int32_t candidates;   /* settings timed */
-  int32_t sweeps;       /* sweeps timed per pair */
-  float best_ms;        /* device time of those sweeps with the chosen pair */
-  float entry_ms;       /* and with the pair the context had on entry */
+  int32_t sweeps;       /* sweeps timed per setting (gsl_autotune), max_iters (gsl_autotune_batch) */
+  float best_ms;        /* device time with the chosen setting */
+  float entry_ms;       /* and with the setting the context had on entry */
+  int32_t majority;     /* own-label majority mode (gsl_ctx_set_majority) */
+  int32_t blk_threads;  /* block shape (gsl_ctx_set_block_config) */
+  int32_t blk_slots;
 } gsl_tune_result;
 
-/* Autotuner for the degree-class thresholds (the paper has no counterpart:
+/* Autotuner of the sweep kernels' settings (the paper has no counterpart:
  * its CPU design has no degree classes).  Runs the first `sweeps` sweeps
  * of synchronous or asynchronous LPA (mode) from the identity labels on
- * graph g (device CSR, weights as in gsl_lpa) once per candidate setting:
- * warp_max in {128, 256, 512, 1024}, blk_max in {4096, 12288, 32768,
- * 131072} with blk_max >= warp_max (pairs that bin g's vertices alike are
- * timed once), two-phase mode 0 or 1 (gsl_ctx_set_pregather).  Each run is
- * timed with CUDA events on `stream`; the fastest setting is set on the
- * context (the setting the context had on entry wins ties).  1 <= sweeps <= 64.  Labels do not depend on the thresholds, so
- * tuning changes only speed.  The context's scratch is used; the graph
- * is only read.  Synchronises `stream`.  Errors as gsl_lpa; on error the
- * entry thresholds are restored. */
+ * graph g (device CSR, weights as in gsl_lpa) once per candidate setting
+ * and times each run with CUDA events on `stream`.  Candidates: warp_max
+ * in {128, 256, 512, 1024} x blk_max in {4096, 12288, 32768, 131072} with
+ * blk_max >= warp_max, x block shape (threads, table slots) in {(512,
+ * 12288), (256, 6144)}, x majority mode in {0, 1, 2}, x two-phase mode in
+ * {0, 1}; settings that run the same kernels on g (the same binning of
+ * g's degrees, and a block shape or majority mode only where g has rows
+ * that use it) are timed once.  The fastest setting is set on the context
+ * (the setting the context had on entry wins ties).  1 <= sweeps <= 64.
+ * Labels do not depend on any of these settings, so tuning changes only
+ * speed.  The context's scratch is used; the graph is only read.
+ * Synchronises `stream`.  Errors as gsl_lpa; on error the entry setting
+ * is restored. */
 int gsl_autotune(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, int32_t mode, int32_t sweeps,
                  gsl_tune_result* out, void* stream);
+
+/* The same search for the batched path: each candidate setting (as for
+ * gsl_autotune, without two-phase sweeps, which the batched loop does not
+ * use) runs gsl_gsllpa_batch on the packed graphs (arguments as there; a
+ * sample of the graphs a caller will batch), once to capture its CUDA
+ * graph and once timed (gsl_batch_stats.ms).  labels_out receives the
+ * batch's labels (the same for every setting); the fastest setting stays
+ * on the context.  Synchronises `stream`. */
+int gsl_autotune_batch(gsl_ctx* ctx, const gsl_csr* g, int32_t num_graphs, const int64_t* vptr_host,
+                       const int32_t* weights, double tolerance, int32_t max_iters, int32_t mode,
+                       int32_t* labels_out, gsl_tune_result* out, void* stream);
 
 /* Label propagation: lpa() of Algorithm 3 without its final split (the
  * "GVE-LPA" phase).  Labels start as labels_init (device int32[n], values
@@ -292,10 +324,16 @@ int gsl_modularity(gsl_ctx* ctx, const gsl_csr* g, const int32_t* weights, const
  *              GSL_ERR_INVALID without touching the device.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call uses the same array and clears what it needs at its start, so
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race and must be serialised by the caller.  Returns GSL_ERR_INVALID for
- * malformed input detected on the device, GSL_ERR_CUDA for a runtime error. */
+ * The call reads its sums back and waits for `stream` to finish before it
+ * returns.  Every call uses the same array and clears what it needs at its
+ * start, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Returns
+ * GSL_ERR_INVALID for malformed input detected on the device (offsets not
+ * starting at 0, decreasing or not ending at nnz; a column or label outside
+ * [0, n); a weight <= 0) -- the next call starts from cleared sums -- and
+ * GSL_ERR_CUDA for a runtime error of this call's own launches or copies (a
+ * launch error left pending by earlier work on the thread is cleared at
+ * entry). */
 #define GSL_NOALLOC_MAX_N 4194304
 int gsl_modularity_noalloc(const gsl_csr* g, const int32_t* weights, const int32_t* labels,
                            double* q_out, void* stream);

@@ -74,7 +74,8 @@ class ServerStats(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("warp_max", ctypes.c_int32), ("blk_max", ctypes.c_int32), ("pregather", ctypes.c_int32),
                 ("candidates", ctypes.c_int32),
-                ("sweeps", ctypes.c_int32), ("best_ms", ctypes.c_float), ("entry_ms", ctypes.c_float)]
+                ("sweeps", ctypes.c_int32), ("best_ms", ctypes.c_float), ("entry_ms", ctypes.c_float),
+                ("majority", ctypes.c_int32), ("blk_threads", ctypes.c_int32), ("blk_slots", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -116,11 +117,13 @@ def load():
         lib.gsl_ctx_destroy.argtypes = [P]
         lib.gsl_ctx_set_tuning.argtypes = [P, i32, i32]
         lib.gsl_autotune.argtypes = [P, cp, P, i32, i32, ctypes.POINTER(TuneResult), P]
+        lib.gsl_autotune_batch.argtypes = [P, cp, i32, P, P, dbl, i32, i32, P, ctypes.POINTER(TuneResult), P]
         lib.gsl_ctx_set_pregather.argtypes = [P, i32]
         lib.gsl_ctx_set_block_config.argtypes = [P, i32, i32]
         lib.gsl_ctx_set_majority.argtypes = [P, i32]
         lib.gsl_ctx_set_hub_cluster.argtypes = [P, i64]
         lib.gsl_ctx_set_f32_fixed.argtypes = [P, i32]
+        lib.gsl_ctx_set_retry_bounds.argtypes = [P, i32, i32]
         lib.gsl_lpa_f32.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_gsllpa_f32.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
         lib.gsl_modularity_f32.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
@@ -225,6 +228,24 @@ class Context:
                                            ctypes.byref(r), _stream(stream)))
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
+    def autotune_batch(self, offsets, cols, vptr, weights=None, tolerance=0.05, max_iters=20, mode=MODE_SYNC,
+                       out=None, stream=None):
+        """Times the batched path (gsl_gsllpa_batch) under each candidate
+        setting on these packed graphs and sets the fastest on this context;
+        returns (labels, the choice and times)."""
+        import numpy as np
+        import torch
+        g = _check_graph(offsets, cols, weights)
+        vp = np.ascontiguousarray(vptr, dtype=np.int64)
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.int32, device=offsets.device)
+        r = TuneResult()
+        self._raise(self._lib.gsl_autotune_batch(self._h, ctypes.byref(g), int(vp.shape[0] - 1),
+                                                 vp.ctypes.data_as(ctypes.c_void_p), _ptr(weights), float(tolerance),
+                                                 int(max_iters), int(mode), _ptr(out), ctypes.byref(r),
+                                                 _stream(stream)))
+        return out, {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
     def set_block_config(self, threads: int, table_slots: int):
         self._raise(self._lib.gsl_ctx_set_block_config(self._h, int(threads), int(table_slots)))
 
@@ -245,6 +266,12 @@ class Context:
     def set_pregather(self, mode: int):
         """0: never (default), 1: when the frontier is large, 2: every eligible sweep."""
         self._raise(self._lib.gsl_ctx_set_pregather(self._h, int(mode)))
+
+    def set_retry_bounds(self, probe_bound: int = 0, unionfind_bound: int = 0):
+        """Bounds of the device retry loops (hash probes, union-find steps);
+        0 restores the defaults.  A loop that reaches its bound makes the call
+        fail with GSL_ERR_TIMEOUT."""
+        self._raise(self._lib.gsl_ctx_set_retry_bounds(self._h, int(probe_bound), int(unionfind_bound)))
 
     def set_batch_mode(self, use_cuda_graph: bool):
         self._raise(self._lib.gsl_ctx_set_batch_mode(self._h, int(bool(use_cuda_graph))))

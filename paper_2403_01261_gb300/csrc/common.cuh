@@ -39,6 +39,7 @@ struct Counters {
   unsigned int hub_clu_next;               // the next of those rows to be taken
   unsigned int pad3;
   unsigned int uns_count[NCLASS];          // majority filter: rows left for the table kernels
+  unsigned int phase_cls[NCLASS];          // asynchronous sweeps: cls_count of the sweep's first phase
   int err;                      // ERRBIT_* (sticky for the call)
   int pad1;
   // per-graph data filled by the class histogram

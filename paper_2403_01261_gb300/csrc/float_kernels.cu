@@ -84,9 +84,9 @@ __device__ __forceinline__ double group_sum(unsigned m, float w) {
 // Adds c to label lbl's sum in an open-addressing table of cap slots.
 template <bool GLOBAL>
 __device__ __forceinline__ void fslot_add(unsigned* keys, double* vals, unsigned cap, unsigned lbl, double c,
-                                          int* err) {
+                                          int* err, int probe_cap) {
   unsigned h = __umulhi(hash32(lbl), cap);
-  for (int p = 0; p < PROBE_CAP; ++p) {
+  for (int p = 0; p < probe_cap; ++p) {
     unsigned k = GLOBAL ? __ldcg(keys + h) : *(volatile unsigned*)(keys + h);
     if (k == EMPTY32) k = atomicCAS(keys + h, EMPTY32, lbl);
     if (k == EMPTY32 || k == lbl) {
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(F_BLOCK) sweep_f_block_kernel(SweepArgs a, con
       const unsigned m = __match_any_sync(FULL, lbl);
       const double sum = group_sum(m, w);
       if (lbl >= 0 && (m & lanemask_lt()) == 0) {
-        if (global) fslot_add<true>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
-        else fslot_add<false>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
+        if (global) fslot_add<true>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err, a.probe_cap);
+        else fslot_add<false>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err, a.probe_cap);
       }
     }
     for (int o = 16; o; o >>= 1) own_acc += __shfl_xor_sync(FULL, own_acc, o);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(F_WARP_BLOCK) sweep_f_warp_kernel(SweepArgs a,
       if (__ballot_sync(FULL, lbl >= 0) == 0) continue;
       const unsigned m = __match_any_sync(FULL, lbl);
       const double sum = group_sum(m, w);
-      if (lbl >= 0 && (m & lanemask_lt()) == 0) fslot_add<false>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err);
+      if (lbl >= 0 && (m & lanemask_lt()) == 0) fslot_add<false>(keys, vals, cap, (unsigned)lbl, sum, &a.ctr->err, a.probe_cap);
     }
     __syncwarp();
     double bs = -1.0;

@@ -340,6 +340,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
   a.col = g->cols;
   a.w = weights;
   a.ctr = c->ctr;
+  a.probe_cap = c->tune.probe_cap;
   a.work = c->work;
   a.wtab = c->wtab;
   a.wtab_region = 2ll * c->tune.warp_max;
@@ -371,11 +372,6 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
       c->profile.slot[SL_IDENT].entries += g->nnz;
       c->profile.slot[SL_IDENT].bytes += 4.0 * (double)g->nnz + 16.0 * (double)n;
       all_active = false;   // the bin pass below picks up the flagged rows only
-    }
-    {
-      const int pe = prof_begin(c, s);
-      CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s));
-      prof_end(c, pe, SL_BIN, s, 1);
     }
     if (async_mode) {
       a.prev = c->lab[0];
@@ -416,29 +412,45 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     // (sweep 2 reads the labels of sweep 1, which are nearly all distinct):
     // filter those out before the tables
     const bool filter = !a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
-    SweepArgs af = a;   // classes 7 and 8 after the filter read its worklist
-    if (filter) {
+    if (filter)
       if (int r = grow(c, c->work2, c->cap_work2, n)) return r;
-      const int pe = prof_begin(c, s);
-      CK(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, s));
-      prof_end(c, pe, SL_FILTER, s, 2);
-      af.work = c->work2;
-    }
-    for (int k = NCLASS - 1; k >= 0; --k) {   // the longest rows first
-      const int pe = prof_begin(c, s);
-      if (k == CLS_WARP_L || k == CLS_BLOCK) {
-        CK(launch_sweep_class(af, k, weights != nullptr, async_mode, c->tune, c->di, s));
-        prof_end(c, pe, SL_SWEEP0 + k, s, 1);
-      } else if (k == CLS_HUB && c->hub_ready) {
-        HubPlan hp{c->hub_piece_start, c->hub_ustart, c->hub_best, c->hub_own,
-                   c->hub_wsum,        c->hub_used_cnt, c->hub_used, c->hub_tab, c->hub_clu};
-        c->hub_dirty = true;   // until this sweep is known to have finished cleanly
-        int kernels = 0;
-        CK(launch_hub_pieces(a, hp, weights != nullptr, async_mode, filter, c->tune, c->di, s, &kernels));
-        prof_end(c, pe, SL_SWEEP0 + k, s, kernels);
-      } else {
-        CK(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, s));
-        prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+    // An asynchronous sweep runs its frontier in two phases chosen by a hash
+    // of the vertex id and the sweep number, the second reading the labels
+    // the first wrote: neighbours that would update at the same moment every
+    // sweep (and swap labels forever) fall in different phases half of the
+    // time.  A synchronous sweep is one phase.
+    const int phases = async_mode ? 2 : 1;
+    for (int ph = 0; ph < phases; ++ph) {
+      if (ph == 1) CK(launch_phase_reset(c->ctr, nullptr, s));
+      {
+        const int pe = prof_begin(c, s);
+        CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s, nullptr,
+                      nullptr, nullptr, async_mode ? ph : -1, (unsigned)t));
+        prof_end(c, pe, SL_BIN, s, 1);
+      }
+      SweepArgs af = a;   // classes 7 and 8 after the filter read its worklist
+      if (filter) {
+        const int pe = prof_begin(c, s);
+        CK(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, s));
+        prof_end(c, pe, SL_FILTER, s, 2);
+        af.work = c->work2;
+      }
+      for (int k = NCLASS - 1; k >= 0; --k) {   // the longest rows first
+        const int pe = prof_begin(c, s);
+        if (k == CLS_WARP_L || k == CLS_BLOCK) {
+          CK(launch_sweep_class(af, k, weights != nullptr, async_mode, c->tune, c->di, s));
+          prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+        } else if (k == CLS_HUB && c->hub_ready) {
+          HubPlan hp{c->hub_piece_start, c->hub_ustart, c->hub_best, c->hub_own,
+                     c->hub_wsum,        c->hub_used_cnt, c->hub_used, c->hub_tab, c->hub_clu};
+          c->hub_dirty = true;   // until this sweep is known to have finished cleanly
+          int kernels = 0;
+          CK(launch_hub_pieces(a, hp, weights != nullptr, async_mode, filter, c->tune, c->di, s, &kernels));
+          prof_end(c, pe, SL_SWEEP0 + k, s, kernels);
+        } else {
+          CK(launch_sweep_class(a, k, weights != nullptr, async_mode, c->tune, c->di, s));
+          prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+        }
       }
     }
     CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
@@ -454,7 +466,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
       long long act_all = 0;
       for (int k = 0; k < NCLASS; ++k) {
         auto& sl = c->profile.slot[SL_SWEEP0 + k];
-        const long long v = c->ctr_h->cls_count[k];
+        const long long v = (long long)(c->ctr_h->cls_count[k] + c->ctr_h->phase_cls[k]);
         const long long e = (long long)c->ctr_h->cls_scanned[k];
         sl.vertices += v;
         sl.entries += e;
@@ -469,7 +481,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
         long long fe = (long long)c->ctr_h->scanned - cls_e;
         for (int k = CLS_WARP_L; k <= CLS_BLOCK; ++k) {
           fe += (long long)c->ctr_h->cls_scanned[k];
-          rows += c->ctr_h->cls_count[k];
+          rows += (long long)(c->ctr_h->cls_count[k] + c->ctr_h->phase_cls[k]);
         }
         auto& sf = c->profile.slot[SL_FILTER];
         sf.vertices += rows;
@@ -485,7 +497,7 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     c->hub_dirty = false;   // every hub's final pass reset the slots its pieces claimed
     const long long dn = (long long)c->ctr_h->dn;
     long long act = (long long)c->ctr_h->fast_active;
-    for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
+    for (int k = 0; k < NCLASS; ++k) act += (long long)(c->ctr_h->cls_count[k] + c->ctr_h->phase_cls[k]);
     scanned += (long long)c->ctr_h->scanned;
     if (st && t <= GSL_STATS_SWEEPS) {
       st->changed[t - 1] = dn;
@@ -529,6 +541,7 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
   a.off = OFF(g);
   a.col = g->cols;
   a.ctr = c->ctr;
+  a.probe_cap = c->tune.probe_cap;
   a.work = c->work;
   a.n = n;
   int t = 0;
@@ -551,11 +564,6 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
       c->profile.slot[SL_IDENT].bytes += 8.0 * (double)g->nnz + 16.0 * (double)n;   // columns, weights
       all_active = false;
     }
-    {
-      const int pe = prof_begin(c, s);
-      CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s));
-      prof_end(c, pe, SL_BIN, s, 1);
-    }
     a.prev = async_mode ? c->lab[0] : c->lab[(t - 1) & 1];
     a.next = async_mode ? c->lab[0] : c->lab[t & 1];
     a.fnext = c->flag[(t + 1) & 1];
@@ -563,19 +571,30 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
     a.mark = (t > 1 && 2 * dn_prev <= n) ? 1 : 0;
     // the own-label majority filter for classes 7 and 8, as in run_lpa
     const bool filter = !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
-    SweepArgs af = a;
-    if (filter) {
+    if (filter)
       if (int r = grow(c, c->work2, c->cap_work2, n)) return r;
-      const int pe = prof_begin(c, s);
-      CK(launch_majority_filter_f32(a, wf, c->work2, async_mode, c->di, s));
-      prof_end(c, pe, SL_FILTER, s, 2);
-      af.work = c->work2;
-    }
-    for (int k = 0; k < NCLASS; ++k) {
-      const int pe = prof_begin(c, s);
-      CK(launch_sweep_f32(k == CLS_WARP_L || k == CLS_BLOCK ? af : a, wf, k, async_mode, c->fkeys, c->fvals, region,
-                          c->di, s));
-      prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+    const int phases = async_mode ? 2 : 1;   // asynchronous sweeps in two phases, as in run_lpa
+    for (int ph = 0; ph < phases; ++ph) {
+      if (ph == 1) CK(launch_phase_reset(c->ctr, nullptr, s));
+      {
+        const int pe = prof_begin(c, s);
+        CK(launch_bin(OFF(g), n, c->flag[t & 1], all_active ? 1 : 0, c->tune, c->work, c->ctr, c->di, s, nullptr,
+                      nullptr, nullptr, async_mode ? ph : -1, (unsigned)t));
+        prof_end(c, pe, SL_BIN, s, 1);
+      }
+      SweepArgs af = a;
+      if (filter) {
+        const int pe = prof_begin(c, s);
+        CK(launch_majority_filter_f32(a, wf, c->work2, async_mode, c->di, s));
+        prof_end(c, pe, SL_FILTER, s, 2);
+        af.work = c->work2;
+      }
+      for (int k = 0; k < NCLASS; ++k) {
+        const int pe = prof_begin(c, s);
+        CK(launch_sweep_f32(k == CLS_WARP_L || k == CLS_BLOCK ? af : a, wf, k, async_mode, c->fkeys, c->fvals,
+                            region, c->di, s));
+        prof_end(c, pe, SL_SWEEP0 + k, s, 1);
+      }
     }
     CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -587,7 +606,7 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
       long long act_all = 0;
       for (int k = 0; k < NCLASS; ++k) {
         auto& sl = c->profile.slot[SL_SWEEP0 + k];
-        const long long v = c->ctr_h->cls_count[k];
+        const long long v = (long long)(c->ctr_h->cls_count[k] + c->ctr_h->phase_cls[k]);
         const long long e = (long long)c->ctr_h->cls_scanned[k];
         sl.vertices += v;
         sl.entries += e;
@@ -600,7 +619,7 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
         long long fe = (long long)c->ctr_h->scanned - cls_e;
         for (int k = CLS_WARP_L; k <= CLS_BLOCK; ++k) {
           fe += (long long)c->ctr_h->cls_scanned[k];
-          rows += c->ctr_h->cls_count[k];
+          rows += (long long)(c->ctr_h->cls_count[k] + c->ctr_h->phase_cls[k]);
         }
         auto& sf = c->profile.slot[SL_FILTER];
         sf.vertices += rows;
@@ -614,7 +633,7 @@ int run_lpa_f32(gsl_ctx* c, const gsl_csr* g, const float* wf, const int32_t* la
     if (int r = map_err(c, c->ctr_h->err, "lpa_f32")) return r;
     const long long dn = (long long)c->ctr_h->dn;
     long long act = (long long)c->ctr_h->fast_active;
-    for (int k = 0; k < NCLASS; ++k) act += c->ctr_h->cls_count[k];
+    for (int k = 0; k < NCLASS; ++k) act += (long long)(c->ctr_h->cls_count[k] + c->ctr_h->phase_cls[k]);
     scanned += (long long)c->ctr_h->scanned;
     if (st && t <= GSL_STATS_SWEEPS) {
       st->changed[t - 1] = dn;
@@ -778,6 +797,7 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
   a.col = g->cols;
   a.w = weights;
   a.ctr = c->ctr;
+  a.probe_cap = c->tune.probe_cap;
   a.work = c->work;
   a.wtab = c->wtab;
   a.wtab_region = 2ll * c->tune.warp_max;
@@ -793,10 +813,7 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
     ck(cudaMemsetAsync(c->dn_graph, 0, sizeof(unsigned) * (size_t)num_graphs, cs));
     // per-slot profiling only when launching directly (not inside a capture)
     const bool prof = c->prof && c->batch_direct;
-    int pe = prof ? prof_begin(c, cs) : -1;
-    ck(launch_bin(OFF(g), n, c->flag[t & 1], t <= 2 ? 1 : 0, c->tune, c->work, c->ctr, c->di, cs, c->gid,
-                  c->done, c->stop));
-    if (prof) prof_end(c, pe, SL_BIN, cs, 1);
+    int pe = -1;
     a.prev = async_mode ? c->lab[0] : c->lab[(t - 1) & 1];
     a.next = async_mode ? c->lab[0] : c->lab[t & 1];
     a.fnext = c->flag[(t + 1) & 1];
@@ -806,18 +823,26 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
     const bool filter = !a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
     a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
     a.spread = (t == 2 && !async_mode) ? 1 : 0;
-    SweepArgs af = a;
-    if (filter) {
+    const int phases = async_mode ? 2 : 1;   // asynchronous sweeps in two phases, as in run_lpa
+    for (int ph = 0; ph < phases; ++ph) {
+      if (ph == 1) ck(launch_phase_reset(c->ctr, c->stop, cs));
       pe = prof ? prof_begin(c, cs) : -1;
-      ck(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, cs));
-      if (prof) prof_end(c, pe, SL_FILTER, cs, 2);
-      af.work = c->work2;
-    }
-    for (int k = 0; k < NCLASS; ++k) {
-      pe = prof ? prof_begin(c, cs) : -1;
-      ck(launch_sweep_class(k == CLS_WARP_L || k == CLS_BLOCK ? af : a, k, weights != nullptr, async_mode, c->tune,
-                            c->di, cs));
-      if (prof) prof_end(c, pe, SL_SWEEP0 + k, cs, 1);
+      ck(launch_bin(OFF(g), n, c->flag[t & 1], t <= 2 ? 1 : 0, c->tune, c->work, c->ctr, c->di, cs, c->gid, c->done,
+                    c->stop, async_mode ? ph : -1, (unsigned)t));
+      if (prof) prof_end(c, pe, SL_BIN, cs, 1);
+      SweepArgs af = a;
+      if (filter) {
+        pe = prof ? prof_begin(c, cs) : -1;
+        ck(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, cs));
+        if (prof) prof_end(c, pe, SL_FILTER, cs, 2);
+        af.work = c->work2;
+      }
+      for (int k = 0; k < NCLASS; ++k) {
+        pe = prof ? prof_begin(c, cs) : -1;
+        ck(launch_sweep_class(k == CLS_WARP_L || k == CLS_BLOCK ? af : a, k, weights != nullptr, async_mode, c->tune,
+                              c->di, cs));
+        if (prof) prof_end(c, pe, SL_SWEEP0 + k, cs, 1);
+      }
     }
     ck(launch_graph_update(t, tol, max_iters, c->vptr, num_graphs, c->dn_graph, c->iters, c->done, c->stop, cs));
   }
@@ -913,73 +938,95 @@ int gsl_ctx_set_tuning(gsl_ctx* c, int32_t warp_max, int32_t blk_max) {
   return GSL_OK;
 }
 
-// Binning signature of a threshold pair on the current graph: two pairs
-// that put every vertex in the same class run the same kernels.
-namespace {
-bool same_binning(const std::vector<long long>& deg_sorted, const gsl::Tuning& a, const gsl::Tuning& b) {
-  auto count_le = [&](long long x) {
-    return (long long)(std::upper_bound(deg_sorted.begin(), deg_sorted.end(), x) - deg_sorted.begin());
-  };
-  const gsl::ClassBounds ca = gsl::class_bounds(a), cb = gsl::class_bounds(b);
-  return count_le(ca.warp_small) == count_le(cb.warp_small) && count_le(ca.warp_max) == count_le(cb.warp_max) &&
-         count_le(ca.blk_max) == count_le(cb.blk_max);
-}
-}  // namespace
+}  // extern "C"
 
-int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t mode, int32_t sweeps,
-                 gsl_tune_result* out, void* stream) {
-  if (!c) return GSL_ERR_INVALID;
-  c->last_error.clear();
-  if (!out) return fail(c, GSL_ERR_INVALID, "out is NULL");
-  if (sweeps < 1 || sweeps > GSL_STATS_SWEEPS) return fail(c, GSL_ERR_INVALID, "need 1 <= sweeps <= 64");
-  if (int r = check_csr(c, g)) return r;
-  if (mode != GSL_MODE_SYNC && mode != GSL_MODE_ASYNC) return fail(c, GSL_ERR_INVALID, "unknown mode");
-  const Tuning entry = c->tune;
-  memset(out, 0, sizeof(*out));
-  out->warp_max = entry.warp_max;
-  out->blk_max = entry.blk_max;
-  out->pregather = entry.pregather;
-  out->sweeps = sweeps;
-  if (g->n == 0) return GSL_OK;
-  DeviceGuard dg(c->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  if (int r = ensure_vertex_scratch(c, g->n)) return r;
-  // sorted degrees (host copy of the offsets) decide which pairs bin alike
+// Candidate settings of the autotuners, for a graph with the given sorted
+// degrees.  Two settings are the same run when they bin every vertex alike
+// and agree on every knob that acts on the classes the graph populates:
+// the block shape only matters with rows above warp_max, the majority
+// filter only with rows in classes 7-8 (warp_small+1 .. blk_max).
+namespace {
+struct TuneSpace {
+  bool pregather;   // also try two-phase sweeps
+};
+
+long long count_le(const std::vector<long long>& deg_sorted, long long x) {
+  return (long long)(std::upper_bound(deg_sorted.begin(), deg_sorted.end(), x) - deg_sorted.begin());
+}
+
+bool same_run(const std::vector<long long>& deg_sorted, const gsl::Tuning& a, const gsl::Tuning& b) {
+  const gsl::ClassBounds ca = gsl::class_bounds(a), cb = gsl::class_bounds(b);
+  const long long n = (long long)deg_sorted.size();
+  if (count_le(deg_sorted, ca.warp_small) != count_le(deg_sorted, cb.warp_small) ||
+      count_le(deg_sorted, ca.warp_max) != count_le(deg_sorted, cb.warp_max) ||
+      count_le(deg_sorted, ca.blk_max) != count_le(deg_sorted, cb.blk_max))
+    return false;
+  if (a.pregather != b.pregather) return false;
+  const bool block_rows = count_le(deg_sorted, ca.warp_max) < n;
+  if (block_rows && (a.blk_block != b.blk_block || a.blk_slots != b.blk_slots)) return false;
+  const bool filter_rows = count_le(deg_sorted, ca.blk_max) > count_le(deg_sorted, ca.warp_small);
+  if (filter_rows && a.majority != b.majority) return false;
+  return true;
+}
+
+std::vector<gsl::Tuning> tune_candidates(const std::vector<long long>& deg_sorted, const gsl::Tuning& entry,
+                                         const TuneSpace& sp, int max_smem) {
+  std::vector<gsl::Tuning> cand{entry};
+  const int shapes[2][2] = {{512, 12288}, {256, 6144}};
+  for (int pg : {0, 1}) {
+    if (pg && !sp.pregather) continue;
+    for (int maj : {1, 0, 2})
+      for (const auto& sh : shapes) {
+        if ((long long)sh[1] * 8 + 1024 > max_smem) continue;
+        for (int wm : {128, 256, 512, 1024})
+          for (int bm : {4096, 12288, 32768, 131072}) {
+            if (bm < wm) continue;
+            gsl::Tuning t = entry;
+            t.warp_max = wm;
+            t.blk_max = bm;
+            t.pregather = pg;
+            t.majority = maj;
+            t.blk_block = sh[0];
+            t.blk_slots = sh[1];
+            bool dup = false;
+            for (const gsl::Tuning& u : cand) dup = dup || same_run(deg_sorted, t, u);
+            if (!dup) cand.push_back(t);
+          }
+      }
+  }
+  return cand;
+}
+
+// Sorted degrees of a device CSR (host copy of the offsets).
+int sorted_degrees(gsl_ctx* c, const gsl_csr* g, cudaStream_t s, std::vector<long long>* deg) {
   std::vector<long long> offs((size_t)g->n + 1);
   CK(cudaMemcpyAsync(offs.data(), g->offsets, sizeof(int64_t) * offs.size(), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  std::vector<long long> deg((size_t)g->n);
-  for (long long v = 0; v < g->n; ++v) deg[(size_t)v] = offs[(size_t)v + 1] - offs[(size_t)v];
-  std::sort(deg.begin(), deg.end());
-  std::vector<Tuning> cand{entry};
-  for (int pg : {0, 1})
-    for (int wm : {128, 256, 512, 1024})
-      for (int bm : {4096, 12288, 32768, 131072}) {
-        if (bm < wm) continue;
-        Tuning t = entry;
-        t.warp_max = wm;
-        t.blk_max = bm;
-        t.pregather = pg;
-        bool dup = false;
-        for (const Tuning& u : cand) dup = dup || (u.pregather == t.pregather && same_binning(deg, t, u));
-        if (!dup) cand.push_back(t);
-      }
-  auto time_one = [&](const Tuning& t, float* ms) -> int {
-    c->tune = t;
-    if (int r = prepare_graph(c, g, s)) return r;
-    int* fin = nullptr;
-    CK(cudaEventRecord(c->ev[0], s));
-    if (int r = run_lpa(c, g, weights, nullptr, 0.0, sweeps, mode, nullptr, s, &fin)) return r;
-    CK(cudaEventRecord(c->ev[1], s));
-    CK(cudaEventSynchronize(c->ev[1]));
-    CK(cudaEventElapsedTime(ms, c->ev[0], c->ev[1]));
-    return GSL_OK;
-  };
-  float ms = 0.f;
+  deg->resize((size_t)g->n);
+  for (long long v = 0; v < g->n; ++v) (*deg)[(size_t)v] = offs[(size_t)v + 1] - offs[(size_t)v];
+  std::sort(deg->begin(), deg->end());
+  return GSL_OK;
+}
+
+void fill_result(const gsl::Tuning& t, gsl_tune_result* out) {
+  out->warp_max = t.warp_max;
+  out->blk_max = t.blk_max;
+  out->pregather = t.pregather;
+  out->majority = t.majority;
+  out->blk_threads = t.blk_block;
+  out->blk_slots = t.blk_slots;
+}
+
+// Times every candidate with time_one (an untimed warm-up run of the entry
+// setting first) and leaves the fastest on the context; on error the entry
+// setting is restored.
+template <typename F>
+int tune_loop(gsl_ctx* c, const std::vector<gsl::Tuning>& cand, gsl_tune_result* out, F&& time_one) {
+  const gsl::Tuning entry = c->tune;
+  float ms = 0.f, best_ms = 0.f;
   int best = 0;
-  float best_ms = 0.f;
   for (size_t k = 0; k < cand.size(); ++k) {
-    if (k == 0) {   // untimed warm-up run with the entry pair
+    if (k == 0) {
       if (int r = time_one(cand[0], &ms)) {
         c->tune = entry;
         return r;
@@ -996,12 +1043,78 @@ int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t m
     }
   }
   c->tune = cand[(size_t)best];
-  out->warp_max = c->tune.warp_max;
-  out->blk_max = c->tune.blk_max;
-  out->pregather = c->tune.pregather;
+  c->batch_key.clear();
+  fill_result(c->tune, out);
   out->candidates = (int32_t)cand.size();
   out->best_ms = best_ms;
   return GSL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int gsl_autotune(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, int32_t mode, int32_t sweeps,
+                 gsl_tune_result* out, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (!out) return fail(c, GSL_ERR_INVALID, "out is NULL");
+  if (sweeps < 1 || sweeps > GSL_STATS_SWEEPS) return fail(c, GSL_ERR_INVALID, "need 1 <= sweeps <= 64");
+  if (int r = check_csr(c, g)) return r;
+  if (mode != GSL_MODE_SYNC && mode != GSL_MODE_ASYNC) return fail(c, GSL_ERR_INVALID, "unknown mode");
+  memset(out, 0, sizeof(*out));
+  fill_result(c->tune, out);
+  out->sweeps = sweeps;
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = ensure_vertex_scratch(c, g->n)) return r;
+  std::vector<long long> deg;
+  if (int r = sorted_degrees(c, g, s, &deg)) return r;
+  const std::vector<Tuning> cand = tune_candidates(deg, c->tune, TuneSpace{true}, c->di.max_smem_optin);
+  return tune_loop(c, cand, out, [&](const Tuning& t, float* ms) -> int {
+    c->tune = t;
+    if (int r = prepare_graph(c, g, s)) return r;
+    int* fin = nullptr;
+    CK(cudaEventRecord(c->ev[0], s));
+    if (int r = run_lpa(c, g, weights, nullptr, 0.0, sweeps, mode, nullptr, s, &fin)) return r;
+    CK(cudaEventRecord(c->ev[1], s));
+    CK(cudaEventSynchronize(c->ev[1]));
+    CK(cudaEventElapsedTime(ms, c->ev[0], c->ev[1]));
+    return GSL_OK;
+  });
+}
+
+int gsl_autotune_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int64_t* vptr_host,
+                       const int32_t* weights, double tol, int32_t max_iters, int32_t mode, int32_t* labels_out,
+                       gsl_tune_result* out, void* stream) {
+  if (!c) return GSL_ERR_INVALID;
+  c->last_error.clear();
+  if (!out) return fail(c, GSL_ERR_INVALID, "out is NULL");
+  if (int r = check_lpa_args(c, g, tol, max_iters, mode, labels_out)) return r;
+  if (num_graphs < 1 || !vptr_host) return fail(c, GSL_ERR_INVALID, "need num_graphs >= 1 and vptr");
+  memset(out, 0, sizeof(*out));
+  fill_result(c->tune, out);
+  out->sweeps = max_iters;
+  if (g->n == 0) return GSL_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<long long> deg;
+  if (int r = sorted_degrees(c, g, s, &deg)) return r;
+  // the batched loop has no two-phase mode
+  const std::vector<Tuning> cand = tune_candidates(deg, c->tune, TuneSpace{false}, c->di.max_smem_optin);
+  return tune_loop(c, cand, out, [&](const Tuning& t, float* ms) -> int {
+    c->tune = t;
+    c->batch_key.clear();
+    // first call captures the sweep loop for this setting; the second, timed, replays it
+    for (int rep = 0; rep < 2; ++rep) {
+      gsl_batch_stats st{};
+      if (int r = gsl_gsllpa_batch(c, g, num_graphs, vptr_host, weights, tol, max_iters, mode, labels_out, nullptr,
+                                   &st, stream))
+        return r;
+      *ms = st.ms;
+    }
+    return GSL_OK;
+  });
 }
 
 int gsl_ctx_set_block_config(gsl_ctx* c, int32_t threads, int32_t table_slots) {
@@ -1036,6 +1149,16 @@ int gsl_ctx_set_hub_cluster(gsl_ctx* c, int64_t max_degree) {
   if (!c) return GSL_ERR_INVALID;
   if (max_degree < 0) return fail(c, GSL_ERR_INVALID, "hub cluster degree must be >= 0");
   c->tune.hub_cluster_max = max_degree > (1ll << 30) ? (1 << 30) : (int)max_degree;
+  return GSL_OK;
+}
+
+int gsl_ctx_set_retry_bounds(gsl_ctx* c, int32_t probe_bound, int32_t unionfind_bound) {
+  if (!c) return GSL_ERR_INVALID;
+  if (probe_bound < 0 || unionfind_bound < 0) return fail(c, GSL_ERR_INVALID, "retry bounds must be >= 0");
+  const Tuning d;
+  c->tune.probe_cap = probe_bound ? probe_bound : d.probe_cap;
+  c->tune.uf_cap = unionfind_bound ? unionfind_bound : d.uf_cap;
+  c->batch_key.clear();   // the captured batched loop holds the old bound
   return GSL_OK;
 }
 
@@ -1350,7 +1473,8 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
                                       num_graphs, max_iters, mode, (long long)(tol * 1e12), c->ctr_h->max_degree,
                                       (long long)c->lab[0], (long long)c->wtab, (long long)c->btab,
                                       c->tune.warp_max, c->tune.blk_max, (long long)c->work2,
-                                      c->tune.majority, c->tune.blk_block, c->tune.blk_slots};
+                                      c->tune.majority, c->tune.blk_block, c->tune.blk_slots, c->tune.probe_cap,
+                                      c->tune.uf_cap};
   long long graph_launches = 0;
   if (n > 0) {
     if (c->batch_direct) {

@@ -41,10 +41,11 @@ constexpr int HUB_DSM_PROBES = 128;        // probe bound of the distributed tab
 
 // Global-table insert that records every slot it claims in `used`.
 __device__ __forceinline__ unsigned hub_slot_add(unsigned long long* tab, unsigned cap, unsigned lbl, unsigned c,
-                                                 unsigned* used, unsigned* used_cnt, long long tab_base, int* err) {
+                                                 unsigned* used, unsigned* used_cnt, long long tab_base, int* err,
+                                                 int probe_cap) {
   unsigned h = __umulhi(hash32(lbl), cap);
   const unsigned long long mine = ((unsigned long long)lbl << 32) | c;
-  for (int p = 0; p < PROBE_CAP; ++p) {
+  for (int p = 0; p < probe_cap; ++p) {
     unsigned long long x = __ldcg(tab + h);
     if (x == EMPTY64) {
       x = atomicCAS(tab + h, EMPTY64, mine);
@@ -255,7 +256,8 @@ __device__ __forceinline__ void cluster_row(const SweepArgs& a, int v, int own, 
           const bool leader = l[u] >= 0 && (m & lanemask_lt()) == 0;
           if (GLOBAL) {
             if (leader) {
-              const unsigned sum = hub_slot_add(gtab, gcap, (unsigned)l[u], c, gused, gused_cnt, gbase, &a.ctr->err);
+              const unsigned sum = hub_slot_add(gtab, gcap, (unsigned)l[u], c, gused, gused_cnt, gbase, &a.ctr->err,
+                                                         a.probe_cap);
               const unsigned long long k = pack_key(sum, l[u]);
               best = k > best ? k : best;
             }
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(512, 2) hub_piece_kernel(SweepArgs a, HubPlan 
       const unsigned lbl = st.keys[k];
       if (lbl == EMPTY32) continue;
       const unsigned sum = hub_slot_add(tab, gcap, lbl, st.sums[k], hp.used + hp.ustart[i], hp.used_cnt + i,
-                                        2 * hp.ustart[i], &a.ctr->err);
+                                        2 * hp.ustart[i], &a.ctr->err, a.probe_cap);
       const unsigned long long key = pack_key(sum, (int)lbl);
       best = key > best ? key : best;
     }

@@ -34,6 +34,7 @@ struct SweepArgs {
   int spread;                // labels read are nearly all distinct (sweep 2 from the identity labelling)
   unsigned* kw;              // weighted degree per vertex of classes 6-9: written in sweep 1 (check), then read by
                              // the early stops of the majority filter and the hub clusters (null: none)
+  int probe_cap;             // bound on the probes of one hash-table insert (past it: ERRBIT_TIMEOUT)
 };
 
 struct Tuning {
@@ -47,6 +48,8 @@ struct Tuning {
   int pregather = 0;         // two-phase sweeps: 0 never, 1 when the frontier is large, 2 always
   int majority = 1;          // own-label majority pass: 0 never, 1 once labels settle, 2 always
   int hub_cluster_max = 1 << 30;  // hubs up to this degree go to one thread-block cluster each (0: never)
+  int probe_cap = 1 << 24;   // bound on the probes of one hash-table insert
+  int uf_cap = 1 << 26;      // bound on the steps of one union-find find or union
 };
 
 // Degree bounds of the classes (see common.cuh).
@@ -64,9 +67,14 @@ struct DeviceInfo {
 // lpa_kernels.cu
 cudaError_t launch_class_histogram(const long long* off, long long n, long long nnz, const Tuning& t,
                                    Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+// phase >= 0: only the frontier vertices of that phase of an asynchronous
+// sweep (a hash of the vertex id and `seed`); the others keep their flags.
 cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, int all_active,
                        const Tuning& t, int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s,
-                       const int* gid = nullptr, const unsigned char* done = nullptr, const int* stop = nullptr);
+                       const int* gid = nullptr, const unsigned char* done = nullptr, const int* stop = nullptr,
+                       int phase = -1, unsigned seed = 0);
+// Between the two phases of an asynchronous sweep (see Counters::phase_cls).
+cudaError_t launch_phase_reset(Counters* ctr, const int* stop, cudaStream_t s);
 cudaError_t launch_sweep(const SweepArgs& a, bool weighted, bool async_mode, const Tuning& t,
                          const DeviceInfo& di, cudaStream_t s);
 cudaError_t launch_sweep_class(const SweepArgs& a, int cls, bool weighted, bool async_mode, const Tuning& t,

@@ -83,15 +83,32 @@ __global__ void class_starts_kernel(Counters* ctr) {
 }
 
 // ---------------------------------------------------------------------------
+// Phase of vertex v in the asynchronous sweep with seed `seed` (the sweep
+// number): the top bit of a mixed hash, so that two neighbours fall in the
+// same phase of a sweep with probability 1/2, independently from sweep to
+// sweep.
+__device__ __forceinline__ int sweep_phase(long long v, unsigned seed) {
+  unsigned h = (unsigned)v * 0x9E3779B1u + seed * 0x85EBCA6Bu;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return (int)(h >> 31);
+}
+
 // Frontier binning: every vertex with its flag set (or every vertex when
 // all_active) is appended to its class region; the flag is cleared, which
-// leaves the flag array zeroed for reuse as the frontier after next.
+// leaves the flag array zeroed for reuse as the frontier after next.  With
+// phase >= 0 only the vertices of that phase (sweep_phase) are taken; the
+// flags of the others stay set for the binning of the other phase.
 constexpr int BIN_ITEMS = 8;
 
 __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ off, long long n,
                                                    unsigned char* __restrict__ fcur, int all_active, ClassBounds cb,
                                                    int* __restrict__ work, Counters* ctr, const int* __restrict__ gid,
-                                                   const unsigned char* __restrict__ done, const int* stop) {
+                                                   const unsigned char* __restrict__ done, const int* stop, int phase,
+                                                   unsigned seed) {
   if (stop && *(volatile const int*)stop) return;
   __shared__ unsigned cnt[NCLASS];
   __shared__ unsigned base[NCLASS];
@@ -107,7 +124,12 @@ __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ 
       cls[k] = -1;
       if (v < n) {
         bool act = all_active != 0;
-        if (!act && fcur[v]) { act = true; fcur[v] = 0; }
+        if (act) {
+          if (phase >= 0 && sweep_phase(v, seed) != phase) act = false;
+        } else if (fcur[v] && (phase < 0 || sweep_phase(v, seed) == phase)) {
+          act = true;
+          fcur[v] = 0;
+        }
         if (act && gid && done[gid[v]]) act = false;   // batched: this vertex's graph has stopped
         if (act) cls[k] = degree_class(off[v + 1] - off[v], cb.warp_small, cb.warp_max, cb.blk_max);
       }
@@ -334,7 +356,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
         const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
         bool created = false;
         if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
-          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
           const unsigned long long k = pack_key(sum, l[u]);
           best = k > best ? k : best;
         }
@@ -975,13 +997,33 @@ cudaError_t launch_class_histogram(const long long* off, long long n, long long 
 
 cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, int all_active, const Tuning& t,
                        int* work, Counters* ctr, const DeviceInfo& di, cudaStream_t s, const int* gid,
-                       const unsigned char* done, const int* stop) {
+                       const unsigned char* done, const int* stop, int phase, unsigned seed) {
   if (n <= 0) return cudaSuccess;
   const long long tile = 256ll * BIN_ITEMS;
   long long blocks = (n + tile - 1) / tile;
   const long long cap = 8ll * di.sm_count;
   bin_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr,
-                                                                 gid, done, stop);
+                                                                 gid, done, stop, phase, seed);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Between the two phases of an asynchronous sweep: the first phase's class
+// counts move to phase_cls and the per-phase worklist counters restart.
+__global__ void phase_reset_kernel(Counters* ctr, const int* stop) {
+  if (stop && *(volatile const int*)stop) return;
+  for (int k = 0; k < NCLASS; ++k) {
+    ctr->phase_cls[k] += ctr->cls_count[k];
+    ctr->cls_count[k] = 0;
+    ctr->uns_count[k] = 0;
+  }
+  ctr->hub_pieces = 0;
+  ctr->hub_clusters = 0;
+  ctr->hub_clu_next = 0;
+}
+
+cudaError_t launch_phase_reset(Counters* ctr, const int* stop, cudaStream_t s) {
+  phase_reset_kernel<<<1, 1, 0, s>>>(ctr, stop);
   count_launches(1);
   return cudaGetLastError();
 }

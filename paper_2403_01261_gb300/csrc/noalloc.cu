@@ -184,6 +184,9 @@ extern "C" int gsl_modularity_noalloc(const gsl_csr* g, const int32_t* weights, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = 8 * (sms > 0 ? sms : 1);
+  // A launch error left pending by earlier, unrelated work on this thread is
+  // cleared here, so that the check after the launches sees only this call's.
+  cudaGetLastError();
   na_clear_kernel<<<grid, 256, 0, s>>>(scratch, n);
   if (weights)
     na_rows_kernel<true><<<grid, 256, 0, s>>>(off, g->cols, weights, labels, n, g->nnz, scratch);

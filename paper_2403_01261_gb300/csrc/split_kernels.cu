@@ -28,10 +28,8 @@ namespace gsl {
 
 namespace {
 
-constexpr int UF_CAP = 1 << 26;
-
-__device__ __forceinline__ int uf_find(int* p, int x, int* err) {
-  for (int it = 0; it < UF_CAP; ++it) {
+__device__ __forceinline__ int uf_find(int* p, int x, int* err, int cap) {
+  for (int it = 0; it < cap; ++it) {
     const int px = __ldcg(p + x);
     if (px == x) return x;
     const int ppx = __ldcg(p + px);
@@ -42,10 +40,10 @@ __device__ __forceinline__ int uf_find(int* p, int x, int* err) {
   return x;
 }
 
-__device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err) {
-  for (int it = 0; it < UF_CAP; ++it) {
-    a = uf_find(p, a, err);
-    b = uf_find(p, b, err);
+__device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err, int cap) {
+  for (int it = 0; it < cap; ++it) {
+    a = uf_find(p, a, err, cap);
+    b = uf_find(p, b, err, cap);
     if (a == b) return;
     const int hi = a > b ? a : b, lo = a > b ? b : a;
     const int old = atomicCAS(p + hi, hi, lo);
@@ -62,14 +60,14 @@ constexpr int SPLIT_SCAN = 8;     // row entries the sampling pass looks at for 
 // Offers entry e of u's row to the union-find if it is an intra-community
 // edge; returns whether it was one.
 __device__ __forceinline__ bool hook_entry(const int* col, const int* labels, int* p, long long n, int u, int cu,
-                                           long long e, int* err) {
+                                           long long e, int* err, int cap) {
   const int j = ld_stream(col + e);
   if ((unsigned)j >= (unsigned)n) {
     raise_err(err, ERRBIT_INVALID);
     return false;
   }
   if (j == u || ld_label_ro(labels + j) != cu) return false;
-  uf_unite(p, u, j, err);
+  uf_unite(p, u, j, err, cap);
   return true;
 }
 
@@ -77,7 +75,7 @@ __device__ __forceinline__ bool hook_entry(const int* col, const int* labels, in
 // j's parent is ru, u and j already share a tree (trees only merge), so the
 // union is skipped without walking either path.
 __device__ __forceinline__ void hook_entry_flat(const int* col, const int* labels, int* p, long long n, int u,
-                                                int cu, int ru, long long e, int* err) {
+                                                int cu, int ru, long long e, int* err, int cap) {
   const int j = ld_stream(col + e);
   if ((unsigned)j >= (unsigned)n) {
     raise_err(err, ERRBIT_INVALID);
@@ -85,7 +83,7 @@ __device__ __forceinline__ void hook_entry_flat(const int* col, const int* label
   }
   if (j == u || ld_label_ro(labels + j) != cu) return;
   if (__ldcg(p + j) == ru) return;
-  uf_unite(p, u, j, err);
+  uf_unite(p, u, j, err, cap);
 }
 
 }  // namespace
@@ -100,7 +98,7 @@ __global__ void init_parent_kernel(int* __restrict__ p, long long n) {
 // The first two entries' columns and labels are requested together; the
 // rest of the scan (when they are not both links) goes one entry at a time.
 __global__ void sample_link_kernel(const long long* __restrict__ off, const int* __restrict__ col,
-                                   const int* __restrict__ labels, int* p, long long n, Counters* ctr) {
+                                   const int* __restrict__ labels, int* p, long long n, Counters* ctr, int cap) {
   static_assert(SPLIT_SAMPLE == 2, "the first two entries are loaded together");
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
     const long long s = off[u], e = off[u + 1];
@@ -113,22 +111,22 @@ __global__ void sample_link_kernel(const long long* __restrict__ off, const int*
     const int l1 = v1 && j1 != (int)u ? ld_label_ro(labels + j1) : ~cu;
     int linked = 0;
     if (l0 == cu) {
-      uf_unite(p, (int)u, j0, &ctr->err);
+      uf_unite(p, (int)u, j0, &ctr->err, cap);
       ++linked;
     }
     if (l1 == cu) {
-      uf_unite(p, (int)u, j1, &ctr->err);
+      uf_unite(p, (int)u, j1, &ctr->err, cap);
       ++linked;
     }
     for (int k = 2; k < SPLIT_SCAN && linked < SPLIT_SAMPLE && s + k < e; ++k)
-      linked += hook_entry(col, labels, p, n, (int)u, cu, s + k, &ctr->err) ? 1 : 0;
+      linked += hook_entry(col, labels, p, n, (int)u, cu, s + k, &ctr->err, cap) ? 1 : 0;
   }
 }
 
 // Phases 2 and 5: every parent becomes the root.
-__global__ void flatten_kernel(int* p, int* out, long long n, Counters* ctr) {   // out may equal p
+__global__ void flatten_kernel(int* p, int* out, long long n, Counters* ctr, int cap) {   // out may equal p
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
-    out[v] = uf_find(p, (int)v, &ctr->err);
+    out[v] = uf_find(p, (int)v, &ctr->err, cap);
 }
 
 // Phase 3: the most frequent root among 1024 sampled vertices (one block
@@ -172,7 +170,8 @@ __global__ void __launch_bounds__(1024) giant_kernel(const int* p, long long n, 
 template <int G>
 __global__ void __launch_bounds__(256) hook_group_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                                           const int* __restrict__ labels, int* p, long long n,
-                                                          const int* __restrict__ work, Counters* ctr, int cls) {
+                                                          const int* __restrict__ work, Counters* ctr, int cls,
+                                                          int cap) {
   const unsigned cnt = (unsigned)ctr->cls_total[cls];
   const int* w = work + ctr->cls_start[cls];
   const int giant = ctr->giant;
@@ -186,14 +185,15 @@ __global__ void __launch_bounds__(256) hook_group_kernel(const long long* __rest
     const int ru = __ldcg(p + u);
     if (ru == giant) continue;
     const int cu = labels[u];
-    for (long long k = s + SPLIT_SAMPLE + gl; k < e; k += G) hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err);
+    for (long long k = s + SPLIT_SAMPLE + gl; k < e; k += G) hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err, cap);
   }
 }
 
 // Phase 4, classes 8..9: one block per vertex.
 __global__ void __launch_bounds__(512) hook_block_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                                           const int* __restrict__ labels, int* p, long long n,
-                                                          const int* __restrict__ work, Counters* ctr, int cls) {
+                                                          const int* __restrict__ work, Counters* ctr, int cls,
+                                                          int cap) {
   const unsigned cnt = (unsigned)ctr->cls_total[cls];
   const int* w = work + ctr->cls_start[cls];
   const int giant = ctr->giant;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(512) hook_block_kernel(const long long* __rest
     if (ru == giant) continue;
     const int cu = labels[u];
     for (long long k = s + SPLIT_SAMPLE + threadIdx.x; k < e; k += blockDim.x)
-      hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err);
+      hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err, cap);
   }
 }
 
@@ -397,24 +397,24 @@ int grid_for(long long items, int block, const DeviceInfo& di, int per_sm = 8) {
 
 cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels, const int* work,
                          Counters* ctr, int* parent, int* out, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
-  (void)t;
   if (n <= 0) return cudaSuccess;
+  const int cap = t.uf_cap;
   init_parent_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, n);
-  sample_link_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(off, col, labels, parent, n, ctr);
-  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, parent, n, ctr);
+  sample_link_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(off, col, labels, parent, n, ctr, cap);
+  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, parent, n, ctr, cap);
   giant_kernel<<<1, 1024, 0, s>>>(parent, n, ctr);
   const int g = 8 * di.sm_count;
-  hook_group_kernel<1><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 0);
-  hook_group_kernel<2><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 1);
-  hook_group_kernel<4><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 2);
-  hook_group_kernel<8><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 3);
-  hook_group_kernel<16><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 4);
-  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 5);
-  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_S);
-  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_L);
-  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_BLOCK);
-  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_HUB);
-  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr);
+  hook_group_kernel<1><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 0, cap);
+  hook_group_kernel<2><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 1, cap);
+  hook_group_kernel<4><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 2, cap);
+  hook_group_kernel<8><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 3, cap);
+  hook_group_kernel<16><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 4, cap);
+  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 5, cap);
+  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_S, cap);
+  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_L, cap);
+  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_BLOCK, cap);
+  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_HUB, cap);
+  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr, cap);
   count_launches(15);
   return cudaGetLastError();
 }

@@ -9,7 +9,6 @@
 namespace gsl {
 namespace {
 
-constexpr int PROBE_CAP = 1 << 24;        // bound on open-addressing probes
 constexpr unsigned long long EMPTY64 = ~0ull;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -131,9 +130,9 @@ __device__ __forceinline__ SlotTable make_table(unsigned long long* base, long l
 
 template <bool GLOBAL>
 __device__ __forceinline__ unsigned slot_add(SlotTable t, unsigned cap, unsigned lbl, unsigned c, bool& created,
-                                             int* err) {
+                                             int* err, int probe_cap) {
   unsigned h = __umulhi(hash32(lbl), cap);
-  for (int p = 0; p < PROBE_CAP; ++p) {
+  for (int p = 0; p < probe_cap; ++p) {
     unsigned k = GLOBAL ? __ldcg(t.keys + h) : *(volatile unsigned*)(t.keys + h);
     if (k == EMPTY32) {
       k = atomicCAS(t.keys + h, EMPTY32, lbl);
@@ -301,7 +300,7 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
         const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
         bool created = false;
         if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
-          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err);
+          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
           const unsigned long long k = pack_key(sum, l[u]);
           best = k > best ? k : best;
         }
