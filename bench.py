@@ -47,19 +47,21 @@ def parse():
                    help="edge weights: unit (the benchmark), int32 1..32 or float32 k/8 for k in 1..32, "
                         "both from a hash of the endpoint pair (symmetric)")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--cpu-scale", type=int, default=19, help="R-MAT scale of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--cache", default=os.environ.get("GSL_BENCH_CACHE", os.path.join(tempfile.gettempdir(),
-                                                                                    "gsl_bench_cache")))
+    p.add_argument("--cache", default=default_cache())
     p.add_argument("--profile-json", default="", help="also write the per-slot profile here")
     p.add_argument("--workload", choices=["rmat", "batched", "served", "compare"], default="rmat",
                    help="rmat: one R-MAT graph (default); batched: many SBM graphs per call vs one call per graph")
     p.add_argument("--graphs", type=int, default=4096, help="graphs in the batched workload")
     p.add_argument("--gen-procs", type=int, default=0, help="host processes generating the batched graphs")
     p.add_argument("--rate", type=float, default=2000.0, help="served: mean Poisson arrival rate (requests/s)")
-    p.add_argument("--duration", type=float, default=5.0, help="served: seconds of arrivals per rate")
-    p.add_argument("--pool", type=int, default=48, help="served: distinct request graphs (drawn with replacement)")
+    p.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals per rate")
+    p.add_argument("--pool", type=int, default=512, help="served: distinct request graphs (drawn with replacement)")
+    p.add_argument("--line-served-duration", type=float, default=10.0,
+                   help="seconds of arrivals per rate of the served object in the default line")
+    p.add_argument("--no-batched", action="store_true", help="default line without the batched object")
+    p.add_argument("--no-served", action="store_true", help="default line without the served object")
     p.add_argument("--slots", type=int, default=3, help="served: concurrent batches of the server")
     return p.parse_args()
 
@@ -90,13 +92,21 @@ def replicas_value(world, units_per_rank, ms):
 
 
 # ------------------------------------------------------------------ workload
+def workload_paths(scale, edge_factor, cache):
+    """The .npy files (offsets, cols) of the cached R-MAT workload graph."""
+    tag = f"rmat{scale}_ef{edge_factor}_s1"
+    return os.path.join(cache, tag + "_offsets.npy"), os.path.join(cache, tag + "_cols.npy")
+
+
+def default_cache():
+    return os.environ.get("GSL_BENCH_CACHE", os.path.join(tempfile.gettempdir(), "gsl_bench_cache"))
+
+
 def workload_graph(scale, edge_factor, cache, rank, world):
     """R-MAT graph, generated once per machine and cached as .npy files."""
     import numpy as np
     import inputs as I
-    tag = f"rmat{scale}_ef{edge_factor}_s1"
-    off_p = os.path.join(cache, tag + "_offsets.npy")
-    col_p = os.path.join(cache, tag + "_cols.npy")
+    off_p, col_p = workload_paths(scale, edge_factor, cache)
     if rank == 0 and not (os.path.exists(off_p) and os.path.exists(col_p)):
         os.makedirs(cache, exist_ok=True)
         t0 = time.time()
@@ -194,52 +204,78 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU side
-def cpu_baseline(scale, edge_factor, tol, max_iters):
-    """The oracle as it stands (single thread): full GSL-LPA (synchronous LPA
-    + BFS split) on a smaller R-MAT of the same generator and parameters."""
+def oracle_gsllpa(offsets, cols, tol, max_iters):
+    """The oracle as it stands (single thread): synchronous lpa() of
+    Algorithm 3, then the BFS split of Algorithm 2, timed per phase."""
     import inputs as I
     import oracle as O
-    g = I.rmat(scale, edge_factor, 0.57, 0.19, 0.19, seed=1, permute=True)
+    g = I.Graph(offsets, cols)
     t0 = time.perf_counter()
     lab, t, dn = O.lpa_sync(g, tol, max_iters)
     t1 = time.perf_counter()
-    O.split_bfs(g, lab)
+    split = O.split_bfs(g, lab)
     t2 = time.perf_counter()
-    return {
-        "value": g.nnz / (t2 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": (f"full oracle GSL-LPA (Jacobi LPA tol {tol} max {max_iters}, then BFS split) on R-MAT scale "
-                   f"{scale} ef {edge_factor}, same generator and seed: n={g.n}, nnz={g.nnz}, {t} sweeps, "
-                   f"lpa {t1 - t0:.2f}s split {t2 - t1:.2f}s; the scale-25 graph exceeds the sample budget"),
+    return split, t, dn, t1 - t0, t2 - t1
+
+
+def cpu_baseline(offsets, cols, tol, max_iters, workload, gpu_labels=None, gpu_changed=None):
+    """The oracle on the benchmark's own graph (the whole workload, one
+    thread), beside the GPU result: also reports whether the GPU's labels
+    and per-sweep change counts equal the oracle's."""
+    split, t, dn, lpa_s, split_s = oracle_gsllpa(offsets, cols, tol, max_iters)
+    n, nnz = offsets.shape[0] - 1, cols.shape[0]
+    out = {
+        "value": nnz / (lpa_s + split_s), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": (f"the whole workload ({workload}, n={n}, nnz={nnz}): oracle GSL-LPA (Jacobi LPA tol {tol} "
+                   f"max {max_iters}, then BFS split), {t} sweeps, lpa {lpa_s:.1f}s split {split_s:.1f}s, "
+                   f"one thread"),
         "host_cores": os.cpu_count(),
-        "seconds": t2 - t0,
+        "seconds": lpa_s + split_s,
     }
+    if gpu_labels is not None:
+        import numpy as np
+        out["labels_identical_to_gpu"] = bool(np.array_equal(split, gpu_labels))
+        out["changed_identical_to_gpu"] = list(map(int, dn)) == list(gpu_changed or [])
+    return out
+
+
+REF_SCALE = 21     # R-MAT scale of one reference-arm step
 
 
 def run_reference(args):
+    """The oracle timed as the reference arm: each step is one full oracle
+    GSL-LPA (Jacobi LPA + BFS split, one thread) on an R-MAT graph of the
+    workload's generator and parameters at scale REF_SCALE (1/16 of the
+    scale-25 workload: 25 steps of the full graph would take most of an
+    hour)."""
     rank = rank_env()[0]
     if rank != 0:
         return 0
+    import inputs as I
     import oracle  # noqa: F401  (builds the oracle)
-    vals = []
-    cb = None
+    scale = min(args.scale, REF_SCALE)
+    g = I.rmat(scale, args.edge_factor, 0.57, 0.19, 0.19, seed=1, permute=True)
+    vals, info = [], None
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(min(args.cpu_scale, 18), args.edge_factor, 0.05, 20)
+        _, t, _, lpa_s, split_s = oracle_gsllpa(g.offsets, g.cols, 0.05, 20)
         if i >= args.warmup:
-            vals.append(cb["value"])
+            vals.append(g.nnz / (lpa_s + split_s))
+        info = (t, lpa_s, split_s)
     value = statistics.median(vals) if vals else 0.0
+    sample = (f"per step the oracle's full GSL-LPA (Jacobi LPA tol 0.05 max 20, then BFS split, one thread) on "
+              f"R-MAT scale {scale} ef {args.edge_factor} of the same generator and seed: n={g.n}, nnz={g.nnz}, "
+              f"{info[0] if info else 0} sweeps")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"rmat{args.scale}-ef{args.edge_factor}", "sample_scale": min(args.cpu_scale, 18),
+        "config": {"workload": f"rmat{args.scale}-ef{args.edge_factor}", "sample_scale": scale,
                    "tolerance": 0.05, "max_iters": 20, "mode": "sync"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": cb["sample"] if cb else ""},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
-
 
 
 # ------------------------------------------------------------- batched mode
@@ -264,47 +300,77 @@ def batched_graphs(count, procs):
     return [g for part in parts for g in part]
 
 
-def run_batched(args):
+def pack_graphs(graphs):
+    """Disjoint union of (offsets, cols) pairs as one CSR: (offsets, cols, vptr)."""
     import numpy as np
-    import torch
-    t0 = time.time()
-    graphs = batched_graphs(args.graphs, args.gen_procs)
-    gen_s = time.time() - t0
-    torch.cuda.set_device(0)
-    import paper_2403_01261_gb300 as gsl
-    dev = torch.device("cuda", 0)
     G = len(graphs)
     vptr = np.zeros(G + 1, dtype=np.int64)
     eptr = np.zeros(G + 1, dtype=np.int64)
     for k, (o, c) in enumerate(graphs):
         vptr[k + 1] = vptr[k] + (o.shape[0] - 1)
         eptr[k + 1] = eptr[k] + c.shape[0]
-    n, nnz = int(vptr[-1]), int(eptr[-1])
-    off_u = np.empty(n + 1, dtype=np.int64)
-    col_u = np.empty(nnz, dtype=np.int32)
+    off_u = np.empty(int(vptr[-1]) + 1, dtype=np.int64)
+    col_u = np.empty(int(eptr[-1]), dtype=np.int32)
     off_u[0] = 0
     for k, (o, c) in enumerate(graphs):
         off_u[vptr[k] + 1:vptr[k + 1] + 1] = o[1:] + eptr[k]
         col_u[eptr[k]:eptr[k + 1]] = c + vptr[k]
+    return off_u, col_u, vptr
+
+
+TUNE_SAMPLE = 256    # graphs of the batch the autotuner times its candidates on
+
+
+def batched_bench(count, steps, warmup, gen_procs=0, tune=True):
+    """The batched workload (count planted-partition graphs in one CUDA-graph
+    sweep loop per call) against one gsl_gsllpa call per graph; with `tune`,
+    gsl_autotune_batch first picks the sweep settings on a sample of the
+    graphs and the batch is timed with the defaults and with that choice."""
+    import numpy as np
+    import torch
+    t0 = time.time()
+    graphs = batched_graphs(count, gen_procs)
+    gen_s = time.time() - t0
+    torch.cuda.set_device(0)
+    import paper_2403_01261_gb300 as gsl
+    dev = torch.device("cuda", 0)
+    G = len(graphs)
+    off_u, col_u, vptr = pack_graphs(graphs)
+    n, nnz = int(vptr[-1]), int(col_u.shape[0])
     off_d = torch.from_numpy(off_u).to(dev)
     col_d = torch.from_numpy(col_u).to(dev)
     solo = [(torch.from_numpy(o).to(dev), torch.from_numpy(c).to(dev)) for o, c in graphs]
-    ctx = gsl.Context(0)
-    out = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
-        ctx.gsllpa_batch(off_d, col_d, vptr, out=out)
-    launches0 = gsl.kernel_launches()
+    out = torch.empty(n, dtype=torch.int32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(args.steps):
-            _, iters = ctx.gsllpa_batch(off_d, col_d, vptr, out=out)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-    batch_ms = e0.elapsed_time(e1) / args.steps
-    launches = gsl.kernel_launches() - launches0
+
+    def timed(ctx):
+        for _ in range(warmup):
+            ctx.gsllpa_batch(off_d, col_d, vptr, out=out)
+        l0 = gsl.kernel_launches()
+        with ClockSampler(0) as clk:
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(steps):
+                _, it = ctx.gsllpa_batch(off_d, col_d, vptr, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps, gsl.kernel_launches() - l0, clk.summary(), it
+
+    base_ctx = gsl.Context(0)
+    default_ms, _, _, _ = timed(base_ctx)
+    default_labels = out.cpu().numpy()
+    tuned = None
+    ctx = base_ctx
+    if tune:
+        ctx = gsl.Context(0)
+        ks = max(1, min(G, TUNE_SAMPLE))
+        so, sc, sv = pack_graphs(graphs[:ks])
+        _, tr = ctx.autotune_batch(torch.from_numpy(so).to(dev), torch.from_numpy(sc).to(dev), sv)
+        tuned = {k: tr[k] for k in ("warp_max", "blk_max", "majority", "blk_threads", "blk_slots", "candidates")}
+        tuned.update({"sample_graphs": ks, "sample_entry_ms": tr["entry_ms"], "sample_best_ms": tr["best_ms"]})
+    batch_ms, launches, clocks, iters = timed(ctx)
+    same_as_default = bool(np.array_equal(out.cpu().numpy(), default_labels))
     # per-slot device time of one batch launched directly (outside the timed region)
     ctx.set_batch_mode(False)
     ctx.set_profiling(True)
@@ -312,33 +378,49 @@ def run_batched(args):
     prof_direct = {p["name"]: round(p["ms"], 3) for p in ctx.profile() if p["ms"] > 0}
     ctx.set_profiling(False)
     ctx.set_batch_mode(True)
+    ctx.gsllpa_batch(off_d, col_d, vptr, out=out)
     # one call per graph, graphs resident, same library
+    plain = gsl.Context(0)
     outs = [torch.empty(o.numel() - 1, dtype=torch.int32, device=dev) for o, _ in solo]
     for (o, c), lab in zip(solo[:64], outs[:64]):
-        ctx.gsllpa(o, c, out=lab)
+        plain.gsllpa(o, c, out=lab)
     torch.cuda.synchronize(dev)
     p0 = time.perf_counter()
     e0.record(stream)
     for (o, c), lab in zip(solo, outs):
-        ctx.gsllpa(o, c, out=lab)
+        plain.gsllpa(o, c, out=lab)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plain_ms = max(e0.elapsed_time(e1), (time.perf_counter() - p0) * 1e3)
     ob = out.cpu().numpy()
     same = all(np.array_equal(ob[vptr[k]:vptr[k + 1]], outs[k].cpu().numpy()) for k in range(G))
-    line = {
-        "metric": "batched GSL-LPA graphs/s (4096 SBM graphs, one CUDA-graph sweep loop per batch)",
-        "value": G / (batch_ms * 1e-3), "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"batched-sbm-{G}", "n": n, "nnz": nnz, "tolerance": 0.05, "max_iters": 20,
-                   "mode": "sync", "laws": "n log-uniform [1e3,2e5], blocks U{5..200}, degree U[8,40], ratio U[3,12]"},
+    res = {
+        "value": G / (batch_ms * 1e-3), "unit": "graphs/s", "ms_per_step": batch_ms, "steps": steps,
+        "warmup": warmup, "graphs": G, "n": n, "nnz": nnz,
         "plain": {"value": G / (plain_ms * 1e-3), "unit": "graphs/s", "ms": plain_ms,
                   "how": "one gsl_gsllpa call per graph, graphs resident"},
         "speedup_vs_plain": plain_ms / batch_ms, "labels_identical_to_plain": bool(same),
+        "autotune": tuned, "default_setting_ms": default_ms, "tuned_gain": default_ms / batch_ms,
+        "labels_identical_to_default_setting": same_as_default,
         "edges_per_s": nnz / (batch_ms * 1e-3), "max_sweeps": int(iters.max()), "mean_sweeps": float(iters.mean()),
-        "gpu_launches": launches, "generation_s": gen_s, "clocks": clk.summary(),
-        "profile_direct_ms": prof_direct,
+        "gpu_launches": launches, "generation_s": gen_s, "clocks": clocks, "profile_direct_ms": prof_direct,
+    }
+    for c in (base_ctx, ctx, plain):
+        c.close()
+    return res
+
+
+def run_batched(args):
+    r = batched_bench(args.graphs, args.steps, args.warmup, args.gen_procs)
+    line = {
+        "metric": f"batched GSL-LPA graphs/s ({r['graphs']} SBM graphs, one CUDA-graph sweep loop per batch)",
+        "value": r["value"], "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batched-sbm-{r['graphs']}", "n": r["n"], "nnz": r["nnz"], "tolerance": 0.05,
+                   "max_iters": 20, "mode": "sync",
+                   "laws": "n log-uniform [1e3,2e5], blocks U{5..200}, degree U[8,40], ratio U[3,12]"},
+        **{k: v for k, v in r.items() if k not in ("value", "ms_per_step", "steps", "warmup", "n", "nnz")},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -463,15 +545,16 @@ def _serve_at(srv, pool, rate, duration, seed):
     return picks, infos, labels, t_end - t_start
 
 
-def run_served(args):
+def served_bench(pool_size, rate, duration, slots, gen_procs=0):
     """Served workload: Poisson arrivals of request graphs (70 % planted
-    partition, 30 % R-MAT, n log-uniform 1e3..2^22) from a pinned host pool,
-    through the library's continuous-batching server; against one
-    gsl_gsllpa_host call per request, one at a time."""
+    partition, 30 % R-MAT, n log-uniform 1e3..2^22) drawn from a pinned host
+    pool of pool_size distinct graphs, through the library's
+    continuous-batching server, at the offered rate and at half the achieved
+    rate; against one gsl_gsllpa_host call per request, one at a time."""
     import numpy as np
     import torch
     t0 = time.time()
-    raw = served_pool(args.pool, args.gen_procs)
+    raw = served_pool(pool_size, gen_procs)
     gen_s = time.time() - t0
     torch.cuda.set_device(0)
     import paper_2403_01261_gb300 as gsl
@@ -480,6 +563,7 @@ def run_served(args):
         to, tc = torch.from_numpy(o).pin_memory(), torch.from_numpy(c).pin_memory()
         keep.append((to, tc))
         pool.append((to.numpy(), tc.numpy()))
+    del raw
     # plain: one request at a time through the host-buffer entry point
     ctx = gsl.Context(0)
     outs = [torch.empty(o.shape[0] - 1, dtype=torch.int32).pin_memory() for o, _ in pool]
@@ -491,40 +575,55 @@ def run_served(args):
     plain_s = time.perf_counter() - p0
     plain_gps = len(pool) / plain_s
     ctx.close()
-    srv = gsl.Server(device=0, slots=args.slots, memory_fraction=0.6, tolerance=0.05, max_iters=20)
+    srv = gsl.Server(device=0, slots=slots, memory_fraction=0.6, tolerance=0.05, max_iters=20)
     for k in range(min(4, len(pool))):     # warm-up
         srv.wait(srv.submit(*pool[k]))
     runs = []
     launches0 = gsl.kernel_launches()
-    with ClockSampler(0) as clk:
-        for rate in (args.rate, None):
-            if rate is None:   # a second, lighter load where p99 is not queueing-dominated
-                rate = 0.5 * min(args.rate, runs[0]["achieved_rps"])
-            picks, infos, labels, wall = _serve_at(srv, pool, rate, args.duration, seed=len(runs))
-            lat = np.array([i["latency_ms"] for i in infos])
-            runs.append({"offered_rps": rate, "requests": len(infos), "achieved_rps": len(infos) / wall,
-                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                         "mean_batch_graphs": float(np.mean([i["batch_graphs"] for i in infos])),
-                         "same_as_plain": all(np.array_equal(lab, outs[k].numpy()) for k, lab in labels.items())})
+    clocks = []
+    for rate_k in (rate, None):
+        if rate_k is None:   # a second, lighter load where p99 is not queueing-dominated
+            rate_k = 0.5 * min(rate, runs[0]["achieved_rps"])
+        with ClockSampler(0) as clk:
+            picks, infos, labels, wall = _serve_at(srv, pool, rate_k, duration, seed=len(runs))
+        clocks.append(clk.summary())
+        lat = np.array([i["latency_ms"] for i in infos])
+        que = np.array([i["queue_ms"] for i in infos])
+        svc = np.array([i["service_ms"] for i in infos])
+        runs.append({"offered_rps": rate_k, "requests": len(infos), "achieved_rps": len(infos) / wall,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "queue_p50_ms": float(np.percentile(que, 50)), "service_p50_ms": float(np.percentile(svc, 50)),
+                     "mean_batch_graphs": float(np.mean([i["batch_graphs"] for i in infos])),
+                     "same_as_plain": all(np.array_equal(lab, outs[k].numpy()) for k, lab in labels.items())})
     launches = gsl.kernel_launches() - launches0
     st = srv.stats()
     srv.close()
     nnz = np.array([c.shape[0] for _, c in pool])
-    line = {
-        "metric": "served GSL-LPA graphs/s with p50/p99 latency (Poisson arrivals, continuous batching)",
-        "value": runs[0]["achieved_rps"], "unit": "graphs/s", "n_gpus": 1, "steps": len(runs), "warmup": 4,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"served-pool{len(pool)}", "rate_rps": args.rate, "duration_s": args.duration,
-                   "slots": args.slots, "mix": "70% planted partition / 30% R-MAT ef16, n log-uniform 1e3..2^22",
-                   "mean_nnz": float(nnz.mean()), "tolerance": 0.05, "max_iters": 20, "mode": "sync"},
+    return {
+        "value": runs[0]["achieved_rps"], "unit": "graphs/s", "rate_rps": rate, "duration_s": duration,
+        "pool": len(pool), "slots": slots, "mean_nnz": float(nnz.mean()),
         "p50_ms": runs[0]["p50_ms"], "p99_ms": runs[0]["p99_ms"], "runs": runs,
         "plain": {"value": plain_gps, "unit": "graphs/s", "how": "one gsl_gsllpa_host call per pool graph, pinned"},
         "speedup_vs_plain": runs[0]["achieved_rps"] / plain_gps,
+        "max_possible_speedup_at_rate": rate / plain_gps,
         "labels_identical_to_plain": all(r["same_as_plain"] for r in runs),
-        "server": st, "gpu_launches": launches, "generation_s": gen_s, "clocks": clk.summary(),
+        "server": st, "gpu_launches": launches, "generation_s": gen_s, "clocks": clocks,
         "e2e": {"value": runs[0]["achieved_rps"], "unit": "graphs/s",
                 "h2d_bytes_per_step": int(8 * sum(o.shape[0] for o, _ in pool) + 4 * nnz.sum()) // len(pool),
                 "d2h_bytes_per_step": int(4 * sum(o.shape[0] - 1 for o, _ in pool)) // len(pool)},
+    }
+
+
+def run_served(args):
+    r = served_bench(args.pool, args.rate, args.duration, args.slots, args.gen_procs)
+    line = {
+        "metric": "served GSL-LPA graphs/s with p50/p99 latency (Poisson arrivals, continuous batching)",
+        "value": r["value"], "unit": "graphs/s", "n_gpus": 1, "steps": len(r["runs"]), "warmup": 4,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"served-pool{r['pool']}", "rate_rps": args.rate, "duration_s": args.duration,
+                   "slots": args.slots, "mix": "70% planted partition / 30% R-MAT ef16, n log-uniform 1e3..2^22",
+                   "mean_nnz": r["mean_nnz"], "tolerance": 0.05, "max_iters": 20, "mode": "sync"},
+        **{k: v for k, v in r.items() if k not in ("value", "rate_rps", "duration_s", "pool", "slots", "mean_nnz")},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -552,6 +651,28 @@ def dominant_roofline(profile, peaks):
             "frac": achieved / peak, "traffic": traffic, "peak_source": src,
             "bytes_per_launch": top["bytes"] / max(1, top["launches"]),
             "ms_per_launch": top["ms"] / max(1, top["launches"]), "launches": top["launches"]}
+
+
+SPLIT_SLOTS = ("split_unionfind", "split_count_renumber")
+
+
+def phase_roofline(profile, peak, steps, step_ms):
+    """Algorithmic bytes over device time for the whole sweep phase (every
+    slot but the split and modularity) and for the whole step (every slot's
+    bytes over the measured step time)."""
+    sweep = [s for s in profile if s["name"] not in SPLIT_SLOTS and s["name"] != "modularity"]
+    sb = sum(s["bytes"] for s in sweep)
+    sms = sum(s["ms"] for s in sweep)
+    tb = sum(s["bytes"] for s in profile if s["name"] != "modularity")
+    out = {}
+    if sms > 0:
+        a = sb / (sms * 1e-3) / 1e9
+        out["sweep_phase"] = {"achieved": a, "frac": a / peak, "bytes_per_step": sb / steps,
+                              "ms_per_step": sms / steps}
+    if step_ms > 0:
+        a = tb / steps / (step_ms * 1e-3) / 1e9
+        out["step"] = {"achieved": a, "frac": a / peak, "bytes_per_step": tb / steps, "ms_per_step": step_ms}
+    return out
 
 
 def hbm_peak():
@@ -668,11 +789,23 @@ def main():
     split_ms = statistics.median(s["ms_split"] for s in stats)
     peak = hbm_peak()
     roof = dominant_roofline(prof, peak)
+    if roof:
+        roof.update(phase_roofline(prof, peak[0], args.steps, ms))
+    clocks = clk.summary()
+    gpu_labels = out.cpu().numpy()
+    del ctx, off, col, out, wt
+    torch.cuda.empty_cache()
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_scale, args.edge_factor, 0.05, 20)
+        cpu = cpu_baseline(offsets_np, cols_np, 0.05, 20, f"R-MAT scale {args.scale} ef {args.edge_factor}",
+                           gpu_labels if args.weights == "unit" and mode == 0 else None, st["changed"])
         cpu.pop("seconds", None)
-    clocks = clk.summary()
+    extra = {}
+    if world == 1 and not args.no_batched:
+        extra["batched"] = batched_bench(args.graphs, 3, 2, args.gen_procs)
+    if world == 1 and not args.no_served:
+        extra["served"] = served_bench(args.pool, args.rate, args.line_served_duration, args.slots,
+                                       args.gen_procs)
     line = {
         "metric": METRIC, "value": replicas_value(world, nnz, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -686,6 +819,7 @@ def main():
         "edges_scanned_per_s": world * st["edges_scanned"] / (ms * 1e-3),
         "changed": st["changed"], "active": st["active"],
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        **extra,
     }
     if args.profile_json:
         with open(args.profile_json, "w") as f:
