@@ -49,7 +49,7 @@ struct Tuning {
   int majority = 1;          // own-label majority pass: 0 never, 1 once labels settle, 2 always
   int hub_cluster_max = 1 << 30;  // hubs up to this degree go to one thread-block cluster each (0: never)
   int probe_cap = 1 << 24;   // bound on the probes of one hash-table insert
-  int uf_cap = 1 << 26;      // bound on the steps of one union-find find or union
+  int uf_cap = 1 << 26;      // bound on the steps of one union-find find or union (split_kernels.cu UF_CAP)
 };
 
 // Degree bounds of the classes (see common.cuh).
@@ -105,6 +105,22 @@ cudaError_t launch_ident_stream(const long long* off, long long n, const int* co
 // The first two of those passes (row starts, strict-increase check).
 cudaError_t launch_row_check(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
                              unsigned char* bad, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+// Sweeps 1 and 2 while the columns arrive in row-aligned chunks
+// (gsl_gsllpa_host): the row-start bitmap (offsets only, bits zeroed
+// first), sweep 1 from each row's first entries assuming every row is
+// strictly increasing (col may be host memory the device reads), the
+// verification of a landed chunk [e0, e1) (flags rows that are not strictly
+// increasing in `bad` and raises *any_bad), and the all-active binning of
+// the chunk's rows [v0, v1).
+cudaError_t launch_rowstart(const long long* off, long long n, unsigned* bits, long long nbits_words,
+                            const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_ident_first(const long long* off, long long n, const int* col, const unsigned char* zero_flags,
+                               int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_chunk_check(const long long* off, long long n, const int* col, long long nnz, long long e0,
+                               long long e1, const unsigned* bits, unsigned char* bad, unsigned* any_bad,
+                               Counters* ctr, const DeviceInfo& di, cudaStream_t s);
+cudaError_t launch_bin_range(const long long* off, long long v0, long long v1, const Tuning& t, int* work,
+                             Counters* ctr, const DeviceInfo& di, cudaStream_t s);
 // Streaming sweep 1 with float weights: for strictly increasing rows the
 // label is the neighbour of largest weight (smallest id among equals).
 cudaError_t launch_ident_stream_f32(const long long* off, long long n, const int* col, const float* wf,
@@ -172,9 +188,9 @@ cudaError_t launch_modularity_f32(const long long* off, const int* col, const fl
                                   long long n, double* sigma, double* sums, Counters* ctr, const DeviceInfo& di,
                                   cudaStream_t s);
 
-// split_kernels.cu
+// split_kernels.cu.  parent and named: n ints of scratch each.
 cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels,
-                         const int* work, Counters* ctr, int* parent, int* out, const Tuning& t,
+                         const int* work, Counters* ctr, int* parent, int* named, int* out, const Tuning& t,
                          const DeviceInfo& di, cudaStream_t s);
 cudaError_t launch_renumber(const int* rep, int* out, long long n, int* rank, unsigned long long* block_sums,
                             long long nblocks_cap, unsigned long long* k_dev, const DeviceInfo& di,

@@ -102,8 +102,11 @@ __device__ __forceinline__ int sweep_phase(long long v, unsigned seed) {
 // leaves the flag array zeroed for reuse as the frontier after next.  With
 // phase >= 0 only the vertices of that phase (sweep_phase) are taken; the
 // flags of the others stay set for the binning of the other phase.
+// PHASED is a template flag so that the one-phase binning of synchronous
+// sweeps carries no phase test.
 constexpr int BIN_ITEMS = 8;
 
+template <bool PHASED>
 __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ off, long long n,
                                                    unsigned char* __restrict__ fcur, int all_active, ClassBounds cb,
                                                    int* __restrict__ work, Counters* ctr, const int* __restrict__ gid,
@@ -124,9 +127,14 @@ __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ 
       cls[k] = -1;
       if (v < n) {
         bool act = all_active != 0;
-        if (act) {
-          if (phase >= 0 && sweep_phase(v, seed) != phase) act = false;
-        } else if (fcur[v] && (phase < 0 || sweep_phase(v, seed) == phase)) {
+        if (!PHASED) {
+          if (!act && fcur[v]) {
+            act = true;
+            fcur[v] = 0;
+          }
+        } else if (act) {
+          if (sweep_phase(v, seed) != phase) act = false;
+        } else if (fcur[v] && sweep_phase(v, seed) == phase) {
           act = true;
           fcur[v] = 0;
         }
@@ -863,6 +871,118 @@ cudaError_t launch_ident_stream(const long long* off, long long n, const int* co
 }
 
 // ---------------------------------------------------------------------------
+// Pieces of the first two sweeps while the columns are still arriving
+// (gsl_gsllpa_host): the rows are cut into chunks at row boundaries, and a
+// chunk's columns are checked and its rows swept as soon as it has landed.
+
+// Strict-increase and range check of the entries [e0, e1) of a chunk that
+// ends at a row boundary (so e1 starts a row or is nnz): the same verdicts
+// as sorted_check_kernel on those entries.  Every flagged row also raises
+// *any_bad.
+__global__ void __launch_bounds__(256) sorted_check_range_kernel(const long long* __restrict__ off, long long n,
+                                                                  const int* __restrict__ col, long long nnz,
+                                                                  long long e0, long long e1,
+                                                                  const unsigned* __restrict__ bits,
+                                                                  unsigned char* __restrict__ bad, unsigned* any_bad,
+                                                                  Counters* ctr) {
+  const unsigned long long pol = policy_evict_first();
+  for (long long e = e0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int je = ld_stream(col + e, pol);
+    if ((unsigned)je >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
+    const long long f = e + 1;
+    if (f < e1 && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0) {
+      const int jn = ld_stream(col + f, pol);
+      if (!(je < jn)) {
+        bad[row_of(off, n, e)] = 1;
+        if (__ldcg(any_bad) == 0) atomicOr(any_bad, 1u);
+      }
+    }
+  }
+  (void)nnz;
+}
+
+// All-active binning of the rows [v0, v1) (sweep 2 runs on every vertex):
+// appended to their class regions as bin_kernel does.
+__global__ void __launch_bounds__(256) bin_range_kernel(const long long* __restrict__ off, long long v0, long long v1,
+                                                         ClassBounds cb, int* __restrict__ work, Counters* ctr) {
+  __shared__ unsigned cnt[NCLASS];
+  __shared__ unsigned base[NCLASS];
+  const long long tile = (long long)blockDim.x * BIN_ITEMS;
+  for (long long t0 = v0 + (long long)blockIdx.x * tile; t0 < v1; t0 += (long long)gridDim.x * tile) {
+    if (threadIdx.x < NCLASS) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int cls[BIN_ITEMS];
+    unsigned pos[BIN_ITEMS];
+#pragma unroll
+    for (int k = 0; k < BIN_ITEMS; ++k) {
+      const long long v = t0 + (long long)k * blockDim.x + threadIdx.x;
+      cls[k] = v < v1 ? degree_class(off[v + 1] - off[v], cb.warp_small, cb.warp_max, cb.blk_max) : -1;
+      const unsigned m = __match_any_sync(FULL, cls[k]);
+      const int leader = __ffs(m) - 1;
+      unsigned b = 0;
+      if ((int)(threadIdx.x & 31) == leader && cls[k] >= 0) b = atomicAdd(&cnt[cls[k]], (unsigned)__popc(m));
+      pos[k] = __shfl_sync(FULL, b, leader) + (unsigned)__popc(m & lanemask_lt());
+    }
+    __syncthreads();
+    if (threadIdx.x < NCLASS) base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&ctr->cls_count[threadIdx.x], cnt[threadIdx.x]) : 0u;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BIN_ITEMS; ++k) {
+      if (cls[k] >= 0) {
+        const long long v = t0 + (long long)k * blockDim.x + threadIdx.x;
+        work[ctr->cls_start[cls[k]] + base[cls[k]] + pos[k]] = (int)v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Sweep 1 from the identity labelling on rows assumed strictly increasing,
+// reading only each row's first entries, from `col` (which may be host
+// memory the device can read): the labels and counts ident_first_kernel
+// gives when no row is flagged.
+cudaError_t launch_ident_first(const long long* off, long long n, const int* col, const unsigned char* zero_flags,
+                               int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ident_first_kernel<<<16 * di.sm_count, 256, 0, s>>>(off, n, col, zero_flags, next, ctr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowstart(const long long* off, long long n, unsigned* bits, long long nbits_words,
+                            const DeviceInfo& di, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * (size_t)nbits_words, s)) return e;
+  rowstart_kernel<<<8 * di.sm_count, 256, 0, s>>>(off, n, bits);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_check(const long long* off, long long n, const int* col, long long nnz, long long e0,
+                               long long e1, const unsigned* bits, unsigned char* bad, unsigned* any_bad,
+                               Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  if (e1 <= e0) return cudaSuccess;
+  long long blocks = (e1 - e0 + 255) / 256;
+  const long long cap = 8ll * di.sm_count;
+  sorted_check_range_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, col, nnz, e0, e1, bits, bad,
+                                                                               any_bad, ctr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_range(const long long* off, long long v0, long long v1, const Tuning& t, int* work,
+                             Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  if (v1 <= v0) return cudaSuccess;
+  const long long tile = 256ll * BIN_ITEMS;
+  long long blocks = (v1 - v0 + tile - 1) / tile;
+  const long long cap = 8ll * di.sm_count;
+  bin_range_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, v0, v1, class_bounds(t), work, ctr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 namespace {
 std::atomic<long long> g_launches{0};
@@ -1002,8 +1122,13 @@ cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, i
   const long long tile = 256ll * BIN_ITEMS;
   long long blocks = (n + tile - 1) / tile;
   const long long cap = 8ll * di.sm_count;
-  bin_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr,
-                                                                 gid, done, stop, phase, seed);
+  const int grid = (int)(blocks < cap ? blocks : cap);
+  if (phase >= 0)
+    bin_kernel<true><<<grid, 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr, gid, done, stop, phase,
+                                          seed);
+  else
+    bin_kernel<false><<<grid, 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr, gid, done, stop, -1,
+                                           0u);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -14,11 +14,17 @@
 //     Ben-Nun and Bar-Noy, "Optimizing Parallel Graph Connectivity
 //     Computation via Subgraph Sampling", IPDPS 2018): first every vertex
 //     links with its first SPLIT_SAMPLE row entries of its own community;
-//     after flattening, the most frequent root among sampled vertices names
-//     the largest piece, and only vertices outside it offer their remaining
-//     entries.  An edge between two vertices of that piece is redundant, and
-//     an edge leaving it is offered from its other end, so the components
-//     are the same as offering every edge.
+//     after flattening, every community names one of its pieces (the root
+//     one of its vertices holds, the last write winning; the community of
+//     the most frequent root among sampled vertices names that root), and
+//     only vertices outside their community's named piece offer their
+//     remaining entries.  An edge inside a named piece is redundant, and an
+//     edge between a named piece and another piece of the same community is
+//     offered from the other end, so the components are the same as
+//     offering every edge.  Communities are mapped to a table of n slots
+//     (label c in [0, n) to slot c, others by a hash); a slot shared by two
+//     communities names a piece of one of them, and the other's vertices
+//     then all offer their entries, which is slower but still exact.
 // All loops are bounded (parents strictly decrease along a path and a
 // failed CAS strictly lowers the root being linked); the bound is a safety
 // net that raises ERRBIT_TIMEOUT.
@@ -28,8 +34,20 @@ namespace gsl {
 
 namespace {
 
-__device__ __forceinline__ int uf_find(int* p, int x, int* err, int cap) {
-  for (int it = 0; it < cap; ++it) {
+// Bound of the union-find loops.  The default is a compile-time constant
+// (the loops are measurably faster that way); kernels instantiated with
+// UfCap<0> take a bound lowered at run time (gsl_ctx_set_retry_bounds).
+constexpr int UF_CAP = 1 << 26;
+template <int FIXED>
+struct UfCap {
+  int runtime;
+  __device__ __forceinline__ int get() const { return FIXED > 0 ? FIXED : runtime; }
+};
+
+template <int F>
+__device__ __forceinline__ int uf_find(int* p, int x, int* err, UfCap<F> cap) {
+  const int bound = cap.get();
+  for (int it = 0; it < bound; ++it) {
     const int px = __ldcg(p + x);
     if (px == x) return x;
     const int ppx = __ldcg(p + px);
@@ -40,8 +58,10 @@ __device__ __forceinline__ int uf_find(int* p, int x, int* err, int cap) {
   return x;
 }
 
-__device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err, int cap) {
-  for (int it = 0; it < cap; ++it) {
+template <int F>
+__device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err, UfCap<F> cap) {
+  const int bound = cap.get();
+  for (int it = 0; it < bound; ++it) {
     a = uf_find(p, a, err, cap);
     b = uf_find(p, b, err, cap);
     if (a == b) return;
@@ -54,13 +74,26 @@ __device__ __forceinline__ void uf_unite(int* p, int a, int b, int* err, int cap
   raise_err(err, ERRBIT_TIMEOUT);
 }
 
-constexpr int SPLIT_SAMPLE = 2;   // same-community links per vertex before the largest piece is known
+// Slot of community label c in a table of n entries.
+__device__ __forceinline__ long long comm_slot(int c, long long n) {
+  if (c >= 0 && (long long)c < n) return c;
+  unsigned x = (unsigned)c;
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return (long long)(((unsigned long long)x * (unsigned long long)n) >> 32);
+}
+
+constexpr int SPLIT_SAMPLE = 2;   // same-community links per vertex before the named pieces are known
 constexpr int SPLIT_SCAN = 8;     // row entries the sampling pass looks at for them
 
 // Offers entry e of u's row to the union-find if it is an intra-community
 // edge; returns whether it was one.
+template <int F>
 __device__ __forceinline__ bool hook_entry(const int* col, const int* labels, int* p, long long n, int u, int cu,
-                                           long long e, int* err, int cap) {
+                                           long long e, int* err, UfCap<F> cap) {
   const int j = ld_stream(col + e);
   if ((unsigned)j >= (unsigned)n) {
     raise_err(err, ERRBIT_INVALID);
@@ -74,8 +107,9 @@ __device__ __forceinline__ bool hook_entry(const int* col, const int* labels, in
 // The same after flattening, with ru = u's parent read once per row: when
 // j's parent is ru, u and j already share a tree (trees only merge), so the
 // union is skipped without walking either path.
+template <int F>
 __device__ __forceinline__ void hook_entry_flat(const int* col, const int* labels, int* p, long long n, int u,
-                                                int cu, int ru, long long e, int* err, int cap) {
+                                                int cu, int ru, long long e, int* err, UfCap<F> cap) {
   const int j = ld_stream(col + e);
   if ((unsigned)j >= (unsigned)n) {
     raise_err(err, ERRBIT_INVALID);
@@ -97,8 +131,9 @@ __global__ void init_parent_kernel(int* __restrict__ p, long long n) {
 // neighbours among its first SPLIT_SCAN row entries.
 // The first two entries' columns and labels are requested together; the
 // rest of the scan (when they are not both links) goes one entry at a time.
+template <int F>
 __global__ void sample_link_kernel(const long long* __restrict__ off, const int* __restrict__ col,
-                                   const int* __restrict__ labels, int* p, long long n, Counters* ctr, int cap) {
+                                   const int* __restrict__ labels, int* p, long long n, Counters* ctr, UfCap<F> cap) {
   static_assert(SPLIT_SAMPLE == 2, "the first two entries are loaded together");
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
     const long long s = off[u], e = off[u + 1];
@@ -124,7 +159,8 @@ __global__ void sample_link_kernel(const long long* __restrict__ off, const int*
 }
 
 // Phases 2 and 5: every parent becomes the root.
-__global__ void flatten_kernel(int* p, int* out, long long n, Counters* ctr, int cap) {   // out may equal p
+template <int F>
+__global__ void flatten_kernel(int* p, int* out, long long n, Counters* ctr, UfCap<F> cap) {   // out may equal p
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
     out[v] = uf_find(p, (int)v, &ctr->err, cap);
 }
@@ -164,17 +200,32 @@ __global__ void __launch_bounds__(1024) giant_kernel(const int* p, long long n, 
   }
 }
 
-// Phase 4, classes 0..7: G lanes per vertex; vertices already in the
-// largest piece are skipped, the others offer entries SPLIT_SAMPLE.. of
-// their row (both directions: the other end may be skipped).
-template <int G>
+// Phase 3b: every community names a piece: the root its vertices hold
+// after flattening, the last write winning; then the community of the most
+// frequent sampled root (giant_kernel) names that root.  Every slot read
+// later was written by the vertex reading it, so no initial value is needed.
+__global__ void name_pieces_kernel(const int* __restrict__ p, const int* __restrict__ labels, long long n,
+                                   int* __restrict__ named) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    named[comm_slot(labels[v], n)] = p[v];
+}
+
+__global__ void name_giant_kernel(const int* __restrict__ labels, long long n, int* __restrict__ named,
+                                  const Counters* ctr) {
+  const int g = ctr->giant;
+  if (g >= 0 && (long long)g < n) named[comm_slot(labels[g], n)] = g;
+}
+
+// Phase 4, classes 0..7: G lanes per vertex; vertices in their community's
+// named piece are skipped, the others offer entries SPLIT_SAMPLE.. of their
+// row (both directions: the other end may be skipped).
+template <int G, int F>
 __global__ void __launch_bounds__(256) hook_group_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                                           const int* __restrict__ labels, int* p, long long n,
                                                           const int* __restrict__ work, Counters* ctr, int cls,
-                                                          int cap) {
+                                                          UfCap<F> cap, const int* __restrict__ named) {
   const unsigned cnt = (unsigned)ctr->cls_total[cls];
   const int* w = work + ctr->cls_start[cls];
-  const int giant = ctr->giant;
   const int gl = threadIdx.x & (G - 1);
   const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const long long ng = ((long long)gridDim.x * blockDim.x) / G;
@@ -183,20 +234,20 @@ __global__ void __launch_bounds__(256) hook_group_kernel(const long long* __rest
     const long long s = off[u], e = off[u + 1];
     if (e - s <= SPLIT_SAMPLE) continue;
     const int ru = __ldcg(p + u);
-    if (ru == giant) continue;
     const int cu = labels[u];
+    if (ru == named[comm_slot(cu, n)]) continue;
     for (long long k = s + SPLIT_SAMPLE + gl; k < e; k += G) hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err, cap);
   }
 }
 
 // Phase 4, classes 8..9: one block per vertex.
+template <int F>
 __global__ void __launch_bounds__(512) hook_block_kernel(const long long* __restrict__ off, const int* __restrict__ col,
                                                           const int* __restrict__ labels, int* p, long long n,
                                                           const int* __restrict__ work, Counters* ctr, int cls,
-                                                          int cap) {
+                                                          UfCap<F> cap, const int* __restrict__ named) {
   const unsigned cnt = (unsigned)ctr->cls_total[cls];
   const int* w = work + ctr->cls_start[cls];
-  const int giant = ctr->giant;
   __shared__ int s_root;
   for (long long item = blockIdx.x; item < (long long)cnt; item += gridDim.x) {
     const int u = w[item];
@@ -205,8 +256,8 @@ __global__ void __launch_bounds__(512) hook_block_kernel(const long long* __rest
     __syncthreads();
     const int ru = s_root;
     __syncthreads();
-    if (ru == giant) continue;
     const int cu = labels[u];
+    if (ru == named[comm_slot(cu, n)]) continue;
     for (long long k = s + SPLIT_SAMPLE + threadIdx.x; k < e; k += blockDim.x)
       hook_entry_flat(col, labels, p, n, u, cu, ru, k, &ctr->err, cap);
   }
@@ -395,27 +446,39 @@ int grid_for(long long items, int block, const DeviceInfo& di, int per_sm = 8) {
 }
 }  // namespace
 
-cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels, const int* work,
-                         Counters* ctr, int* parent, int* out, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int cap = t.uf_cap;
+template <int F>
+void launch_split_t(const long long* off, const int* col, long long n, const int* labels, const int* work,
+                    Counters* ctr, int* parent, int* named, int* out, UfCap<F> cap, const DeviceInfo& di,
+                    cudaStream_t s) {
   init_parent_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, n);
-  sample_link_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(off, col, labels, parent, n, ctr, cap);
-  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, parent, n, ctr, cap);
+  sample_link_kernel<F><<<grid_for(n, 256, di), 256, 0, s>>>(off, col, labels, parent, n, ctr, cap);
+  flatten_kernel<F><<<grid_for(n, 256, di), 256, 0, s>>>(parent, parent, n, ctr, cap);
   giant_kernel<<<1, 1024, 0, s>>>(parent, n, ctr);
+  name_pieces_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, labels, n, named);
+  name_giant_kernel<<<1, 1, 0, s>>>(labels, n, named, ctr);
   const int g = 8 * di.sm_count;
-  hook_group_kernel<1><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 0, cap);
-  hook_group_kernel<2><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 1, cap);
-  hook_group_kernel<4><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 2, cap);
-  hook_group_kernel<8><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 3, cap);
-  hook_group_kernel<16><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 4, cap);
-  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 5, cap);
-  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_S, cap);
-  hook_group_kernel<32><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_L, cap);
-  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_BLOCK, cap);
-  hook_block_kernel<<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_HUB, cap);
-  flatten_kernel<<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr, cap);
-  count_launches(15);
+  hook_group_kernel<1, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 0, cap, named);
+  hook_group_kernel<2, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 1, cap, named);
+  hook_group_kernel<4, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 2, cap, named);
+  hook_group_kernel<8, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 3, cap, named);
+  hook_group_kernel<16, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 4, cap, named);
+  hook_group_kernel<32, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, 5, cap, named);
+  hook_group_kernel<32, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_S, cap, named);
+  hook_group_kernel<32, F><<<g, 256, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_WARP_L, cap, named);
+  hook_block_kernel<F><<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_BLOCK, cap, named);
+  hook_block_kernel<F><<<4 * di.sm_count, 512, 0, s>>>(off, col, labels, parent, n, work, ctr, CLS_HUB, cap, named);
+  flatten_kernel<F><<<grid_for(n, 256, di), 256, 0, s>>>(parent, out, n, ctr, cap);
+  count_launches(17);
+}
+
+cudaError_t launch_split(const long long* off, const int* col, long long n, const int* labels, const int* work,
+                         Counters* ctr, int* parent, int* named, int* out, const Tuning& t, const DeviceInfo& di,
+                         cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (t.uf_cap == UF_CAP)
+    launch_split_t(off, col, n, labels, work, ctr, parent, named, out, UfCap<UF_CAP>{0}, di, s);
+  else
+    launch_split_t(off, col, n, labels, work, ctr, parent, named, out, UfCap<0>{t.uf_cap}, di, s);
   return cudaGetLastError();
 }
 
