@@ -437,11 +437,29 @@ int gsl_server_destroy(gsl_server* server);
 /* gsl_gsllpa on HOST buffers: copies offsets, cols and weights (nullable) to
  * the device, runs GSL-LPA and copies the labels back to labels_out_host
  * (host int32[n]).  Device copies of the graph are context scratch.  Host
- * buffers may be pageable or pinned (pinned is faster). */
+ * buffers may be pageable or pinned (pinned is faster).  Labels and
+ * statistics are those of gsl_gsllpa.
+ *
+ * With pinned cols (cudaHostAlloc / cudaHostRegister), unit weights,
+ * synchronous mode and at least gsl_ctx_set_host_overlap entries, the
+ * column copy overlaps the first two sweeps.  The columns travel in
+ * row-aligned chunks on a context-owned copy stream.  Sweep 1 is evaluated
+ * first from each row's first entries, read by the device straight from the
+ * pinned buffer, assuming every row is strictly increasing.  Each chunk is
+ * then checked, and its rows swept a second time, as soon as it lands.  If a
+ * row turns out not to be strictly increasing, the call redoes GSL-LPA on
+ * the copied graph, so the result is the same either way.  The call returns
+ * only after every copy has finished. */
 int gsl_gsllpa_host(gsl_ctx* ctx, int64_t n, int64_t nnz, const int64_t* offsets_host,
                     const int32_t* cols_host, const int32_t* weights_host, double tolerance,
                     int32_t max_iters, int32_t mode, int32_t* labels_out_host, gsl_stats* stats,
                     void* stream);
+
+/* Smallest number of CSR entries from which gsl_gsllpa_host overlaps its
+ * column copy with the first two sweeps (default 2^24; 0 never; the paper
+ * has no counterpart).  Results do not depend on it.  min_entries < 0:
+ * GSL_ERR_INVALID. */
+int gsl_ctx_set_host_overlap(gsl_ctx* ctx, int64_t min_entries);
 
 /* Profiling.  When enabled on a context, every launch sequence of the
  * context is bracketed by CUDA events on the call's stream and its device

@@ -124,6 +124,7 @@ def load():
         lib.gsl_ctx_set_hub_cluster.argtypes = [P, i64]
         lib.gsl_ctx_set_f32_fixed.argtypes = [P, i32]
         lib.gsl_ctx_set_retry_bounds.argtypes = [P, i32, i32]
+        lib.gsl_ctx_set_host_overlap.argtypes = [P, i64]
         lib.gsl_lpa_f32.argtypes = [P, cp, P, P, dbl, i32, i32, P, sp, P]
         lib.gsl_gsllpa_f32.argtypes = [P, cp, P, dbl, i32, i32, P, sp, P]
         lib.gsl_modularity_f32.argtypes = [P, cp, P, P, ctypes.POINTER(dbl), P]
@@ -272,6 +273,12 @@ class Context:
         0 restores the defaults.  A loop that reaches its bound makes the call
         fail with GSL_ERR_TIMEOUT."""
         self._raise(self._lib.gsl_ctx_set_retry_bounds(self._h, int(probe_bound), int(unionfind_bound)))
+
+    def set_host_overlap(self, min_entries: int):
+        """Entries from which gsllpa_host overlaps its column copy with the
+        first two sweeps (pinned columns, unit weights, synchronous mode);
+        0: never."""
+        self._raise(self._lib.gsl_ctx_set_host_overlap(self._h, int(min_entries)))
 
     def set_batch_mode(self, use_cuda_graph: bool):
         self._raise(self._lib.gsl_ctx_set_batch_mode(self._h, int(bool(use_cuda_graph))))

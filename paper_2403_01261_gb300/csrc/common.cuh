@@ -41,6 +41,7 @@ struct Counters {
   unsigned int uns_count[NCLASS];          // majority filter: rows left for the table kernels
   unsigned int phase_cls[NCLASS];          // asynchronous sweeps: cls_count of the sweep's first phase
   int err;                      // ERRBIT_* (sticky for the call)
+  unsigned any_bad;             // host-buffer overlap: a landed row is not strictly increasing (sticky)
   int pad1;
   // per-graph data filled by the class histogram
   unsigned long long cls_total[NCLASS];  // all vertices per class

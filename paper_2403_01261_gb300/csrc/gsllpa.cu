@@ -93,6 +93,11 @@ struct gsl_ctx {
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
+  // host-buffer path: column chunks copied on their own stream
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> chunk_ev;
+  long long host_overlap_min = 1ll << 24;   // entries from which gsl_gsllpa_host overlaps copies and sweeps
+
   // batched mode
   int* gid = nullptr;
   long long cap_gid = 0;
@@ -320,15 +325,28 @@ int reset_sweep_counters(gsl_ctx* c, cudaStream_t s) {
   return GSL_OK;
 }
 
+// State of a synchronous sweep loop whose first `done` sweeps ran elsewhere
+// (the host-buffer path runs sweeps 1 and 2 while the columns arrive): the
+// labels of sweep `done` are in lab[done & 1], the frontier flags are as
+// that sweep left them, and the per-sweep statistics up to it are filled.
+struct LpaResume {
+  int done;              // sweeps already run
+  bool converged;        // the stop test already held after sweep `done`
+  bool marked_prev;      // sweep `done` marked the neighbours of changed vertices
+  long long dn_prev;     // its change count
+  long long scanned;     // entries read by those sweeps
+};
+
 // The sweep loop.  On success *final points at the scratch buffer holding
 // the labels.  prepare_graph must have run.
 int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t* labels_init, double tol,
-            int32_t max_iters, int32_t mode, gsl_stats* st, cudaStream_t s, int** final) {
+            int32_t max_iters, int32_t mode, gsl_stats* st, cudaStream_t s, int** final,
+            const LpaResume* resume = nullptr) {
   const long long n = g->n;
   const bool async_mode = mode == GSL_MODE_ASYNC;
-  CK(cudaMemsetAsync(c->flag[0], 0, (size_t)n, s));
-  CK(cudaMemsetAsync(c->flag[1], 0, (size_t)n, s));
-  {
+  if (!resume) {
+    CK(cudaMemsetAsync(c->flag[0], 0, (size_t)n, s));
+    CK(cudaMemsetAsync(c->flag[1], 0, (size_t)n, s));
     const int pe = prof_begin(c, s);
     CK(launch_init_labels(labels_init, c->lab[0], async_mode ? nullptr : c->lab[1], n, c->ctr, c->di, s));
     prof_end(c, pe, SL_INIT, s, 1);
@@ -351,11 +369,11 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     if (int r = grow(c, c->kw, c->cap_kw, n)) return r;
     a.kw = c->kw;
   }
-  int t = 0;
-  bool converged = false, marked_prev = false;
-  long long dn_prev = n;
-  long long scanned = 0;
-  while (t < max_iters) {
+  int t = resume ? resume->done : 0;
+  bool converged = resume ? resume->converged : false, marked_prev = resume ? resume->marked_prev : false;
+  long long dn_prev = resume ? resume->dn_prev : n;
+  long long scanned = resume ? resume->scanned : 0;
+  while (t < max_iters && !converged) {
     ++t;
     if (int r = reset_sweep_counters(c, s)) return r;
     bool all_active = t == 1 || !marked_prev;
@@ -692,8 +710,10 @@ int run_split(gsl_ctx* c, const gsl_csr* g, const int32_t* labels_in, int32_t* l
   c->profile.slot[SL_BIN].vertices += n;
   c->profile.slot[SL_BIN].bytes += 20.0 * (double)n;
   pe = prof_begin(c, s);
-  CK(launch_split(OFF(g), g->cols, n, labels_in, c->work, c->ctr, c->parent, labels_out, c->tune, c->di, s));
-  prof_end(c, pe, SL_SPLIT, s, 15);
+  // c->rank is free until the renumbering below: it holds the named pieces
+  CK(launch_split(OFF(g), g->cols, n, labels_in, c->work, c->ctr, c->parent, c->rank, labels_out, c->tune, c->di,
+                  s));
+  prof_end(c, pe, SL_SPLIT, s, 17);
   // per vertex: parent init, own label, offsets, compress read and label
   // write; per entry: the column and, for the half with j < u, the label
   c->profile.slot[SL_SPLIT].vertices += n;
@@ -920,6 +940,8 @@ int gsl_ctx_destroy(gsl_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->evpool) cudaEventDestroy(e);
+  for (auto& e : c->chunk_ev) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bptrs[] = {c->gid, c->vptr, c->dn_graph, c->iters, c->done, c->stop, c->lab_tmp};
@@ -1532,6 +1554,217 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
   return GSL_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr int HOST_CHUNKS = 16;   // row-aligned column chunks of the overlapped host-buffer path
+
+// gsl_gsllpa on host buffers with the column copy overlapped by the first
+// two sweeps (synchronous mode, unit weights, pinned columns the device can
+// read).  The offsets are copied first.  The columns then travel to the
+// device in HOST_CHUNKS row-aligned chunks on the context's copy stream.
+// Meanwhile sweep 1 is evaluated from each row's first entries, read from
+// host memory, on the premise that every row is strictly increasing (then
+// the smallest neighbour other than the vertex wins, as in the streaming
+// first sweep).  As each chunk lands, its entries are checked (range, and
+// the premise) and its rows run sweep 2.  Once every chunk has landed, a
+// row that broke the premise sends the call back to the plain path on the
+// copied graph.  Otherwise sweeps 3.. and the split follow as usual, so the
+// labels and statistics are those of gsl_gsllpa.  *handled stays false
+// when the call does not qualify (the caller takes the plain path).
+int gsllpa_host_overlapped(gsl_ctx* c, int64_t n, int64_t nnz, const int64_t* offsets_host, const int32_t* cols_host,
+                           double tol, int32_t max_iters, int32_t* labels_out_host, gsl_stats* st, cudaStream_t s,
+                           bool* handled) {
+  *handled = false;
+  if (c->host_overlap_min <= 0 || nnz < c->host_overlap_min || max_iters < 1 || c->prof) return GSL_OK;
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, cols_host) != cudaSuccess) {
+    cudaGetLastError();
+    return GSL_OK;
+  }
+  if (pa.type != cudaMemoryTypeHost || !pa.devicePointer) return GSL_OK;   // pageable: plain path
+  const int* cols_dev_view = static_cast<const int*>(pa.devicePointer);
+  // row-aligned chunks of about nnz / HOST_CHUNKS entries each, from the host
+  // offsets; their bounds must be in range before any copy is issued (the
+  // plain path validates malformed offsets on the device and reports them)
+  if (offsets_host[0] != 0 || offsets_host[n] != nnz) return GSL_OK;
+  std::vector<long long> vb{0};
+  for (int k = 1; k < HOST_CHUNKS; ++k) {
+    const long long target = nnz * k / HOST_CHUNKS;
+    const long long v = (long long)(std::lower_bound(offsets_host, offsets_host + n + 1, (int64_t)target) - offsets_host);
+    if (v > vb.back() && v < n) vb.push_back(v);
+  }
+  vb.push_back(n);
+  const int K = (int)vb.size() - 1;
+  for (int k = 0; k < K; ++k)
+    if (offsets_host[vb[k]] < 0 || offsets_host[vb[k + 1]] < offsets_host[vb[k]] || offsets_host[vb[k + 1]] > nnz)
+      return GSL_OK;
+  *handled = true;
+  {
+    const gsl_csr gh{n, nnz, offsets_host, cols_host};
+    if (int r = check_lpa_args(c, &gh, tol, max_iters, GSL_MODE_SYNC, labels_out_host)) return r;
+  }
+  if (int r = grow(c, c->st_off, c->cap_st_off, n + 1)) return r;
+  if (int r = grow(c, c->st_col, c->cap_st_col, nnz)) return r;
+  if (int r = grow(c, c->st_lab, c->cap_st_lab, n)) return r;
+  if (int r = ensure_vertex_scratch(c, n)) return r;
+  const long long words = (nnz >> 5) + 1;
+  if (int r = grow(c, c->rowbits, c->cap_rowbits, words)) return r;
+  if (!c->copy_stream) CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  while ((int)c->chunk_ev.size() < HOST_CHUNKS) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->chunk_ev.push_back(e);
+  }
+  gsl_csr g{n, nnz, reinterpret_cast<const int64_t*>(c->st_off), c->st_col};
+  CK(cudaEventRecord(c->ev[0], s));
+  CK(cudaMemcpyAsync(c->st_off, offsets_host, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
+  // the copies: the copy stream waits for the previous work on s (st_col may
+  // still be read there); every return below waits for the copies first, so
+  // that none is still reading the caller's buffers
+  CK(cudaEventRecord(c->ev[3], s));
+  CK(cudaStreamWaitEvent(c->copy_stream, c->ev[3], 0));
+  struct CopyWait {
+    cudaStream_t cs;
+    ~CopyWait() {
+      if (cudaStreamSynchronize(cs) != cudaSuccess) cudaGetLastError();
+    }
+  } copy_wait{c->copy_stream};
+  for (int k = 0; k < K; ++k) {
+    const long long e0 = offsets_host[vb[k]], e1 = offsets_host[vb[k + 1]];
+    if (e1 > e0)
+      CK(cudaMemcpyAsync(c->st_col + e0, cols_host + e0, sizeof(int32_t) * (size_t)(e1 - e0), cudaMemcpyHostToDevice,
+                         c->copy_stream));
+    CK(cudaEventRecord(c->chunk_ev[(size_t)k], c->copy_stream));
+  }
+  // offsets: validated and classified (synchronises s; the copies go on)
+  if (int r = prepare_graph(c, &g, s)) return r;
+  CK(cudaMemsetAsync(c->flag[0], 0, (size_t)n, s));
+  CK(cudaMemsetAsync(c->flag[1], 0, (size_t)n, s));
+  CK(launch_init_labels(nullptr, c->lab[0], c->lab[1], n, c->ctr, c->di, s));
+  CK(launch_rowstart(OFF(&g), n, c->rowbits, words, c->di, s));
+  // sweep 1 from the first entries of the rows, read from host memory
+  if (int r = reset_sweep_counters(c, s)) return r;
+  CK(launch_ident_first(OFF(&g), n, cols_dev_view, c->flag[0], c->lab[1], c->ctr, c->di, s));
+  CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const long long dn1 = (long long)c->ctr_h->dn, act1 = (long long)c->ctr_h->fast_active;
+  const long long scan1 = (long long)c->ctr_h->scanned;
+  const bool stop1 = (double)dn1 / (double)n <= tol || max_iters == 1;
+  // sweep 2 chunk by chunk as the columns land (every chunk is checked in any case)
+  if (int r = reset_sweep_counters(c, s)) return r;
+  SweepArgs a{};
+  a.off = OFF(&g);
+  a.col = g.cols;
+  a.w = nullptr;
+  a.ctr = c->ctr;
+  a.probe_cap = c->tune.probe_cap;
+  a.work = c->work;
+  a.wtab = c->wtab;
+  a.wtab_region = 2ll * c->tune.warp_max;
+  a.btab = c->btab;
+  a.btab_region = 2ll * c->ctr_h->max_degree;
+  a.n = n;
+  a.prev = c->lab[1];
+  a.next = c->lab[0];
+  a.fnext = c->flag[1];
+  a.gthresh = 3 * c->tune.blk_slots;   // as run_lpa's sweep 2
+  a.spread = 1;
+  a.mark = 2 * dn1 <= n ? 1 : 0;
+  const bool filter = c->tune.majority == 2;
+  if (filter)
+    if (int r = grow(c, c->work2, c->cap_work2, n)) return r;
+  if (!stop1) c->hub_dirty = true;
+  for (int k = 0; k < K; ++k) {
+    CK(cudaStreamWaitEvent(s, c->chunk_ev[(size_t)k], 0));
+    const long long e0 = offsets_host[vb[k]], e1 = offsets_host[vb[k + 1]];
+    CK(launch_chunk_check(OFF(&g), n, g.cols, nnz, e0, e1, c->rowbits, c->flag[0], &c->ctr->any_bad, c->ctr, c->di,
+                          s));
+    if (stop1) continue;
+    if (k > 0) CK(launch_phase_reset(c->ctr, nullptr, s));
+    CK(launch_bin_range(OFF(&g), vb[k], vb[k + 1], c->tune, c->work, c->ctr, c->di, s));
+    SweepArgs af = a;
+    if (filter) {
+      CK(launch_majority_filter(a, c->work2, false, false, c->di, s));
+      af.work = c->work2;
+    }
+    for (int cls = NCLASS - 1; cls >= 0; --cls) {
+      if (cls == CLS_WARP_L || cls == CLS_BLOCK) {
+        CK(launch_sweep_class(af, cls, false, false, c->tune, c->di, s));
+      } else if (cls == CLS_HUB && c->hub_ready) {
+        HubPlan hp{c->hub_piece_start, c->hub_ustart, c->hub_best, c->hub_own,
+                   c->hub_wsum,        c->hub_used_cnt, c->hub_used, c->hub_tab, c->hub_clu};
+        int kernels = 0;
+        CK(launch_hub_pieces(a, hp, false, false, filter, c->tune, c->di, s, &kernels));
+      } else {
+        CK(launch_sweep_class(a, cls, false, false, c->tune, c->di, s));
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(c->ctr_h, c->ctr, offsetof(Counters, pad1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (int r = map_err(c, c->ctr_h->err, "lpa")) return r;
+  if (c->ctr_h->any_bad) {
+    // a row is not strictly increasing: the first sweep's premise failed
+    if (st) memset(st, 0, sizeof(*st));
+    if (int r = gsl_gsllpa(c, &g, nullptr, tol, max_iters, GSL_MODE_SYNC, c->st_lab, st, s)) return r;
+    CK(cudaMemcpyAsync(labels_out_host, c->st_lab, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GSL_OK;
+  }
+  c->hub_dirty = false;
+  LpaResume rs{};
+  rs.done = 1;
+  rs.converged = (double)dn1 / (double)n <= tol;
+  rs.marked_prev = false;
+  rs.dn_prev = dn1;
+  rs.scanned = scan1;
+  if (st) {
+    st->changed[0] = dn1;
+    st->active[0] = act1;
+  }
+  if (!stop1) {
+    const long long dn2 = (long long)c->ctr_h->dn;
+    long long act2 = (long long)c->ctr_h->fast_active;
+    for (int k = 0; k < NCLASS; ++k) act2 += (long long)(c->ctr_h->cls_count[k] + c->ctr_h->phase_cls[k]);
+    rs.done = 2;
+    rs.converged = (double)dn2 / (double)n <= tol;
+    rs.marked_prev = a.mark != 0;
+    rs.dn_prev = dn2;
+    rs.scanned += (long long)c->ctr_h->scanned;
+    if (st && GSL_STATS_SWEEPS >= 2) {
+      st->changed[1] = dn2;
+      st->active[1] = act2;
+    }
+  }
+  int* fin = nullptr;
+  if (int r = run_lpa(c, &g, nullptr, nullptr, tol, max_iters, GSL_MODE_SYNC, st, s, &fin, &rs)) return r;
+  CK(cudaEventRecord(c->ev[1], s));
+  long long k = 0;
+  if (int r = run_split(c, &g, fin, c->st_lab, 0, &k, s)) return r;
+  CK(cudaEventRecord(c->ev[2], s));
+  CK(cudaMemcpyAsync(labels_out_host, c->st_lab, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    cudaEventElapsedTime(&st->ms_lpa, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&st->ms_split, c->ev[1], c->ev[2]);
+    st->communities = k;
+  }
+  return GSL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsl_ctx_set_host_overlap(gsl_ctx* c, int64_t min_entries) {
+  if (!c) return GSL_ERR_INVALID;
+  if (min_entries < 0) return fail(c, GSL_ERR_INVALID, "min_entries must be >= 0");
+  c->host_overlap_min = min_entries;
+  return GSL_OK;
+}
+
 int gsl_gsllpa_host(gsl_ctx* c, int64_t n, int64_t nnz, const int64_t* offsets_host, const int32_t* cols_host,
                     const int32_t* weights_host, double tol, int32_t max_iters, int32_t mode,
                     int32_t* labels_out_host, gsl_stats* st, void* stream) {
@@ -1544,6 +1777,12 @@ int gsl_gsllpa_host(gsl_ctx* c, int64_t n, int64_t nnz, const int64_t* offsets_h
   if (n == 0) return GSL_OK;
   DeviceGuard dg(c->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (!weights_host && mode == GSL_MODE_SYNC) {
+    bool handled = false;
+    const int r = gsllpa_host_overlapped(c, n, nnz, offsets_host, cols_host, tol, max_iters, labels_out_host, st, s,
+                                         &handled);
+    if (handled) return r;
+  }
   if (int r = grow(c, c->st_off, c->cap_st_off, n + 1)) return r;
   if (int r = grow(c, c->st_col, c->cap_st_col, nnz)) return r;
   if (weights_host)

@@ -221,6 +221,58 @@ def test_gsllpa_host_buffers(graph, ctx):
     assert np.array_equal(got.numpy(), want)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_overlap_matches_oracle(graph, ctx, gpu_lib, pinned):
+    """gsl_gsllpa_host with its column copy overlapped by the first two
+    sweeps (the entry threshold lowered to 1, so every graph with pinned
+    columns takes that path; pageable columns take the plain copy): labels,
+    sweep count and per-sweep dN equal the oracle's, also when the run stops
+    after sweep 1 or 2, and the per-sweep frontier sizes equal the device
+    path's."""
+    c = gpu_lib.Context(0)
+    c.set_host_overlap(1)
+    off, col = torch.from_numpy(graph.offsets), torch.from_numpy(graph.cols)
+    if pinned:
+        off, col = off.pin_memory(), col.pin_memory()
+    d_off, d_col, _ = dev(graph)
+    for tol, iters in [(0.05, 20), (0.0, 1), (0.0, 2), (0.0, 3), (1.0, 20)]:
+        want_lpa, t, dn = O.lpa_sync(graph, tol, iters)
+        got, st = c.gsllpa_host(off, col, tolerance=tol, max_iters=iters, stats=True)
+        assert np.array_equal(got.numpy(), O.split_bfs(graph, want_lpa)), (tol, iters)
+        assert st["iterations"] == t and st["changed"] == dn.tolist(), (tol, iters)
+        _, st_dev = ctx.gsllpa(d_off, d_col, tolerance=tol, max_iters=iters, stats=True)
+        assert st["active"] == st_dev["active"] and st["communities"] == st_dev["communities"], (tol, iters)
+
+
+def test_host_overlap_falls_back_on_unsorted_rows(gpu_lib):
+    """Rows that are not strictly increasing (shuffled, with repeated
+    entries) break the first sweep's premise: the overlapped host path
+    notices once the columns have landed and redoes the call on the copied
+    graph, with the oracle's result."""
+    g = I.rmat(13, 16, seed=6)
+    rng = np.random.default_rng(2)
+    cols = g.cols.copy()
+    for v in rng.choice(g.n, 300, replace=False):
+        a, b = g.offsets[v], g.offsets[v + 1]
+        cols[a:b] = rng.permutation(cols[a:b])
+    h = I.Graph(g.offsets, cols, name="rmat13-shuffled")
+    c = gpu_lib.Context(0)
+    c.set_host_overlap(1)
+    want_lpa, t, dn = O.lpa_sync(h, 0.05, 20)
+    got, st = c.gsllpa_host(torch.from_numpy(h.offsets).pin_memory(), torch.from_numpy(h.cols).pin_memory(),
+                            stats=True)
+    assert np.array_equal(got.numpy(), O.split_bfs(h, want_lpa)) and st["changed"] == dn.tolist()
+    with pytest.raises(gpu_lib.GslError):
+        c.set_host_overlap(-1)
+    bad = torch.from_numpy(h.cols.copy())
+    bad[5] = h.n      # an out-of-range column is reported by the chunk check
+    with pytest.raises(gpu_lib.GslError) as e:
+        c.gsllpa_host(torch.from_numpy(h.offsets).pin_memory(), bad.pin_memory())
+    assert e.value.code == 1
+    got = c.gsllpa_host(torch.from_numpy(h.offsets).pin_memory(), torch.from_numpy(h.cols).pin_memory())
+    assert np.array_equal(got.numpy(), O.split_bfs(h, want_lpa))
+
+
 def test_disconnected_fixture_is_repaired(ctx):
     g, rec = load_disconnected40()
     off, col, _ = dev(g)
