@@ -1558,7 +1558,7 @@ int gsl_gsllpa_batch(gsl_ctx* c, const gsl_csr* g, int32_t num_graphs, const int
 
 namespace {
 
-constexpr int HOST_CHUNKS = 16;   // row-aligned column chunks of the overlapped host-buffer path
+constexpr int HOST_CHUNKS = 4;    // row-aligned column chunks of the overlapped host-buffer path (4: fastest of 3..16 on R-MAT 25)
 
 // gsl_gsllpa on host buffers with the column copy overlapped by the first
 // two sweeps (synchronous mode, unit weights, pinned columns the device can
