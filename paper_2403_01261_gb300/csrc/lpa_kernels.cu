@@ -292,7 +292,7 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 // labels are merged with __match_any_sync (label_group) and only the lowest
 // lane of each group inserts.  Returns true (warp-uniform) once more than `limit`
 // distinct labels have been inserted: the table is then abandoned.
-template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
+template <bool WEIGHTED, bool ASYNC, bool GLOBAL, bool SPREAD = false>
 __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
                                          const int* lp, int d,
                                          SlotTable tab, unsigned cap, unsigned limit, const Pol& pol,
@@ -336,7 +336,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
 #pragma unroll
       for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 256 + 32 * u + lane, pol, jn[u], wn[u]);
     }
-    if (!WEIGHTED) {
+    if (!WEIGHTED && !SPREAD) {
       // entries carrying the vertex's own label are counted in registers,
       // the round's four chunks first: once they are more than half of the
       // row's d entries no other label can reach their count, and the rest
@@ -354,16 +354,17 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (e0 + 32 * u < d) {   // warp-uniform: skip empty chunks of short rows
-        if (WEIGHTED) {   // own-label weights summed in registers
+        if (WEIGHTED && !SPREAD) {   // own-label weights summed in registers
           const bool mine = l[u] == own;
           own_sum += __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u);
           if (mine) l[u] = -1;
         }
         if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
-        const unsigned m = label_group(l[u], a.spread);
-        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+        const unsigned m = SPREAD ? 1u << lane : label_group(l[u], a.spread);
+        const unsigned c = SPREAD ? (WEIGHTED ? (unsigned)w[u] : 1u)
+                                  : (WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m));
         bool created = false;
-        if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+        if (l[u] >= 0 && (SPREAD || (m & lanemask_lt()) == 0)) {
           const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
           const unsigned long long k = pack_key(sum, l[u]);
           best = k > best ? k : best;
@@ -383,7 +384,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
 // the warp's region of the global fallback tables (2 * warp_max slots);
 // without it the class bound guarantees 2 d <= TW.  The next vertex's
 // worklist entry and offsets are loaded while the current one is processed.
-template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL>
+template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL, bool SPREAD = false>
 __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(SweepArgs a, int cls) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_w64[];
@@ -428,12 +429,14 @@ __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(Swee
       const unsigned limit = (!SPILL || cap >= want) ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
       unsigned own_sum = 0;
       const int* lp = a.lg ? a.lg + s : nullptr;
-      if (warp_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, lp, d, tab, cap, limit, pol, best, wsum, own_sum) &&
+      if (warp_row<WEIGHTED, ASYNC, false, SPREAD>(a, v, old, cp, wp, lp, d, tab, cap, limit, pol, best, wsum,
+                                                   own_sum) &&
           SPILL) {
         best = 0;
         wsum = 0;
         own_sum = 0;
-        warp_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum, own_sum);
+        warp_row<WEIGHTED, ASYNC, true, SPREAD>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum,
+                                                own_sum);
       }
       __syncwarp();
       if (own_sum) {   // own_sum is warp-uniform
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(Swee
 // after the table is cleared, one after the partial results are published.
 // The worklist entry of the row after next and the offsets and own label
 // of the next row are loaded while the current row is processed.
-template <bool WEIGHTED, bool ASYNC>
+template <bool WEIGHTED, bool ASYNC, bool SPREAD = false>
 __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cls, unsigned tb, int gthresh) {
   if (stopped(a)) return;
   extern __shared__ unsigned long long smem_b64[];
@@ -532,9 +535,10 @@ __global__ void __launch_bounds__(512, 2) sweep_block_kernel(SweepArgs a, int cl
         // raised: at most 4 * threads, within the last quarter of a table of
         // at least 16 * threads slots
         const unsigned limit = cap >= want ? 0xFFFFFFFFu : cap / 4 * 3;
-        ovf = block_row<WEIGHTED, ASYNC, false>(a, v, old, cp, wp, lp, d, stab, cap, limit, pol, sh, par);
+        ovf = block_row<WEIGHTED, ASYNC, false, SPREAD>(a, v, old, cp, wp, lp, d, stab, cap, limit, pol, sh, par);
       }
-      if (ovf) block_row<WEIGHTED, ASYNC, true>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
+      if (ovf)
+        block_row<WEIGHTED, ASYNC, true, SPREAD>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, sh, par);
     }
     unsigned long long b = sh.best[par];
     const unsigned own_sum = sh.own[par];
@@ -999,6 +1003,25 @@ int occupancy_grid(K kernel, int block, size_t smem, const DeviceInfo& di) {
 constexpr int TW_SMALL = 512;    // slots per warp, class 6 (2 d <= 512)
 constexpr int TW_LARGE = 1024;   // slots per warp, class 7
 
+// One warp per row (classes 6 and 7); the grid is sized once per host
+// thread and instantiation from the kernel's occupancy.  With SPILL every
+// warp owns one region of the global fallback tables, which are sized for
+// warp_grid_warps warps: the grid never exceeds that.
+template <bool W, bool A, int TW, bool SPILL, bool SPREAD>
+void launch_warp_class(const SweepArgs& a, int cls, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
+  const size_t smem = (size_t)(t.warp_block / 32) * TW * sizeof(unsigned long long);
+  thread_local int grid = 0;
+  if (!grid) {
+    raise_smem_limit((const void*)sweep_warp_kernel<W, A, TW, SPILL, SPREAD>, smem);
+    grid = occupancy_grid(sweep_warp_kernel<W, A, TW, SPILL, SPREAD>, t.warp_block, smem, di);
+    if (SPILL) {
+      const long long cap = warp_grid_warps(t, di) / (t.warp_block / 32);
+      if (grid > cap) grid = (int)(cap > 0 ? cap : 1);
+    }
+  }
+  sweep_warp_kernel<W, A, TW, SPILL, SPREAD><<<grid, t.warp_block, smem, s>>>(a, cls);
+}
+
 template <bool W, bool A>
 cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const DeviceInfo& di, cudaStream_t s) {
   switch (cls) {
@@ -1016,33 +1039,26 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
     GSL_LAUNCH_GROUP(16, 4)
     GSL_LAUNCH_GROUP(32, 5)
 #undef GSL_LAUNCH_GROUP
-    case CLS_WARP_S: {
-      const size_t smem = (size_t)(t.warp_block / 32) * TW_SMALL * sizeof(unsigned long long);
-      thread_local int grid = 0;
-      if (!grid) {
-        raise_smem_limit((const void*)sweep_warp_kernel<W, A, TW_SMALL, false>, smem);
-        grid = occupancy_grid(sweep_warp_kernel<W, A, TW_SMALL, false>, t.warp_block, smem, di);
-      }
-      sweep_warp_kernel<W, A, TW_SMALL, false><<<grid, t.warp_block, smem, s>>>(a, CLS_WARP_S);
+    case CLS_WARP_S:
+      if (!A && a.spread) launch_warp_class<W, A, TW_SMALL, false, true>(a, CLS_WARP_S, t, di, s);
+      else launch_warp_class<W, A, TW_SMALL, false, false>(a, CLS_WARP_S, t, di, s);
       break;
-    }
-    case CLS_WARP_L: {
-      const size_t smem = (size_t)(t.warp_block / 32) * TW_LARGE * sizeof(unsigned long long);
-      thread_local int grid = 0;
-      if (!grid) {
-        raise_smem_limit((const void*)sweep_warp_kernel<W, A, TW_LARGE, true>, smem);
-        grid = occupancy_grid(sweep_warp_kernel<W, A, TW_LARGE, true>, t.warp_block, smem, di);
-      }
-      sweep_warp_kernel<W, A, TW_LARGE, true><<<grid, t.warp_block, smem, s>>>(a, CLS_WARP_L);
+    case CLS_WARP_L:
+      if (!A && a.spread) launch_warp_class<W, A, TW_LARGE, true, true>(a, CLS_WARP_L, t, di, s);
+      else launch_warp_class<W, A, TW_LARGE, true, false>(a, CLS_WARP_L, t, di, s);
       break;
-    }
     case CLS_BLOCK:
     case CLS_HUB: {
       const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
-      raise_smem_limit((const void*)sweep_block_kernel<W, A>, smem);
       const int grid = (int)block_grid_size(t, di);
-      sweep_block_kernel<W, A><<<grid, t.blk_block, smem, s>>>(a, cls, (unsigned)t.blk_slots,
-                                                               cls == CLS_HUB ? a.gthresh : 0);
+      const int gth = cls == CLS_HUB ? a.gthresh : 0;
+      if (!A && a.spread) {
+        raise_smem_limit((const void*)sweep_block_kernel<W, A, true>, smem);
+        sweep_block_kernel<W, A, true><<<grid, t.blk_block, smem, s>>>(a, cls, (unsigned)t.blk_slots, gth);
+      } else {
+        raise_smem_limit((const void*)sweep_block_kernel<W, A, false>, smem);
+        sweep_block_kernel<W, A, false><<<grid, t.blk_block, smem, s>>>(a, cls, (unsigned)t.blk_slots, gth);
+      }
       break;
     }
     default:

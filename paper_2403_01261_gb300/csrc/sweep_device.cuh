@@ -157,6 +157,13 @@ __device__ __forceinline__ unsigned label_group(int l, int spread) {
   return __match_any_sync(FULL, l);
 }
 
+// Row loops specialised for sweep 2 from the identity labelling (SPREAD):
+// the labels of sweep 1 are nearly all distinct and the vertex's own label
+// is rarely among them, so every lane inserts its own entry (no label
+// match) and the own label goes into the table like any other label (no
+// per-chunk own-label count); the running maximum then covers it, so the
+// result is the same.
+
 }  // namespace
 
 // Per-row values shared by a block.  Rows alternate between two copies, so
@@ -230,7 +237,7 @@ __device__ __forceinline__ void block_publish(const SweepArgs& a, BlockRowShared
 // `limit` the flag is raised and the row is abandoned.  Returns the flag (block-uniform
 // after the closing barrier).  The global-table pass (limit infinite) leaves
 // the flag alone, so every thread still reads the value that sent it there.
-template <bool WEIGHTED, bool ASYNC, bool GLOBAL>
+template <bool WEIGHTED, bool ASYNC, bool GLOBAL, bool SPREAD = false>
 __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
                                          const int* lp, int d,
                                          SlotTable tab, unsigned cap, unsigned limit, const Pol& pol,
@@ -291,15 +298,18 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (r0 + (u * nw + wid) * 32 < d) {   // warp-uniform
-        const bool mine = l[u] == own;
-        own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
-                            : (unsigned)__popc(__ballot_sync(FULL, mine));
-        if (mine) l[u] = -1;
+        if (!SPREAD) {
+          const bool mine = l[u] == own;
+          own_sum += WEIGHTED ? __reduce_add_sync(FULL, mine ? (unsigned)w[u] : 0u)
+                              : (unsigned)__popc(__ballot_sync(FULL, mine));
+          if (mine) l[u] = -1;
+        }
         if (__ballot_sync(FULL, l[u] >= 0) == 0) continue;
-        const unsigned m = label_group(l[u], a.spread);
-        const unsigned c = WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m);
+        const unsigned m = SPREAD ? 1u << lane : label_group(l[u], a.spread);
+        const unsigned c = SPREAD ? (WEIGHTED ? (unsigned)w[u] : 1u)
+                                  : (WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m));
         bool created = false;
-        if (l[u] >= 0 && (m & lanemask_lt()) == 0) {
+        if (l[u] >= 0 && (SPREAD || (m & lanemask_lt()) == 0)) {
           const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
           const unsigned long long k = pack_key(sum, l[u]);
           best = k > best ? k : best;
