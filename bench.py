@@ -590,9 +590,12 @@ def served_bench(pool_size, rate, duration, slots, gen_procs=0):
         lat = np.array([i["latency_ms"] for i in infos])
         que = np.array([i["queue_ms"] for i in infos])
         svc = np.array([i["service_ms"] for i in infos])
+        dev = {k: np.array([i[k] for i in infos]) for k in ("h2d_ms", "compute_ms", "d2h_ms")}
         runs.append({"offered_rps": rate_k, "requests": len(infos), "achieved_rps": len(infos) / wall,
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "queue_p50_ms": float(np.percentile(que, 50)), "service_p50_ms": float(np.percentile(svc, 50)),
+                     "service_mean_ms": float(svc.mean()),
+                     "device_mean_ms": {k: float(v.mean()) for k, v in dev.items()},
                      "mean_batch_graphs": float(np.mean([i["batch_graphs"] for i in infos])),
                      "same_as_plain": all(np.array_equal(lab, outs[k].numpy()) for k, lab in labels.items())})
     launches = gsl.kernel_launches() - launches0

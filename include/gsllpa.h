@@ -410,6 +410,12 @@ typedef struct gsl_request_info {
   double queue_ms;            /* submit -> admitted                                        */
   double service_ms;          /* admitted -> labels on the host                            */
   double latency_ms;          /* submit -> labels on the host                              */
+  /* Device time (CUDA events on the worker's stream) of the batch that
+   * served the request, split into the host-to-device copies, the kernels
+   * (GSL-LPA with its per-sweep host reads) and the label copy back.       */
+  double h2d_ms;
+  double compute_ms;
+  double d2h_ms;
 } gsl_request_info;
 
 typedef struct gsl_server_stats {

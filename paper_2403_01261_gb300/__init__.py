@@ -63,7 +63,8 @@ class ServerConfig(ctypes.Structure):
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("batch_graphs", ctypes.c_int64),
-                ("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("h2d_ms", ctypes.c_double), ("compute_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -501,7 +502,8 @@ class Server:
         lab = out[:n]
         if info:
             return lab, {"sweeps": ri.sweeps, "batch_graphs": ri.batch_graphs, "queue_ms": ri.queue_ms,
-                         "service_ms": ri.service_ms, "latency_ms": ri.latency_ms}
+                         "service_ms": ri.service_ms, "latency_ms": ri.latency_ms, "h2d_ms": ri.h2d_ms,
+                         "compute_ms": ri.compute_ms, "d2h_ms": ri.d2h_ms}
         return lab
 
     def stats(self):

@@ -765,38 +765,50 @@ __device__ __forceinline__ long long row_of(const long long* off, long long n, l
 }
 
 // Entry e (column je) against entry e + 1 (column jn): the row is not
-// strictly increasing if e + 1 continues e's row and jn <= je.
-__device__ __forceinline__ void check_order(const long long* off, long long n, long long nnz, const unsigned* bits,
-                                            unsigned char* bad, long long e, int je, int jn) {
+// strictly increasing if e + 1 continues e's row and jn <= je.  `end` is
+// the end of the checked range, a row boundary (or nnz).  A flagged row
+// also raises *any_bad when it is given.
+__device__ __forceinline__ void check_order(const long long* off, long long n, long long end, const unsigned* bits,
+                                            unsigned char* bad, unsigned* any_bad, long long e, int je, int jn) {
   const long long f = e + 1;
-  if (f < nnz && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0 && !(je < jn)) bad[row_of(off, n, e)] = 1;
+  if (f < end && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0 && !(je < jn)) {
+    bad[row_of(off, n, e)] = 1;
+    if (any_bad && __ldcg(any_bad) == 0) atomicOr(any_bad, 1u);
+  }
 }
 
-__device__ __forceinline__ void check_pair(const long long* off, long long n, long long nnz, const unsigned* bits,
-                                           unsigned char* bad, Counters* ctr, long long e, int je, int jn) {
+__device__ __forceinline__ void check_pair(const long long* off, long long n, long long end, const unsigned* bits,
+                                           unsigned char* bad, unsigned* any_bad, Counters* ctr, long long e, int je,
+                                           int jn) {
   if ((unsigned)je >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
-  check_order(off, n, nnz, bits, bad, e, je, jn);
+  check_order(off, n, end, bits, bad, any_bad, e, je, jn);
 }
 
-// Sixteen entries per thread per round, as four 16-byte loads issued
-// together; the few entries before the first 16-byte boundary and after the
-// last whole quad are checked by one thread.  The entry after a thread's
-// quad comes from the next lane (or the next quad row of the warp).
+// The entries [e0, e1) of a range that ends at a row boundary (the whole
+// array: e0 = 0, e1 = nnz).  Sixteen entries per thread per round, as four
+// 16-byte loads issued together; the few entries before the first 16-byte
+// boundary and after the last whole quad are checked by one thread.  The
+// entry after a thread's quad comes from the next lane (or the next quad
+// row of the warp).  Entry indices (bits, rows, the quads' positions) are
+// absolute.
 __global__ void __launch_bounds__(256) sorted_check_kernel(const long long* __restrict__ off, long long n,
-                                                            const int* __restrict__ col, long long nnz,
+                                                            const int* __restrict__ col, long long e0, long long e1,
                                                             const unsigned* __restrict__ bits,
-                                                            unsigned char* __restrict__ bad, Counters* ctr) {
+                                                            unsigned char* __restrict__ bad, unsigned* any_bad,
+                                                            Counters* ctr) {
   const unsigned long long pol = policy_evict_first();
   const int lane = threadIdx.x & 31;
-  long long head = (long long)((16 - ((unsigned long long)col & 15)) & 15) >> 2;   // col is 4-byte aligned
+  const long long nnz = e1;   // the checked range ends here (a row boundary)
+  long long head = e0 + ((long long)((16 - ((unsigned long long)(col + e0) & 15)) & 15) >> 2);   // 4-byte aligned
   if (head > nnz) head = nnz;
   const long long nq = (nnz - head) >> 2;
   const long long tail0 = head + 4 * nq;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid == 0) {
-    for (long long e = 0; e < head; ++e) check_pair(off, n, nnz, bits, bad, ctr, e, col[e], e + 1 < nnz ? col[e + 1] : 0);
+    for (long long e = e0; e < head; ++e)
+      check_pair(off, n, nnz, bits, bad, any_bad, ctr, e, col[e], e + 1 < nnz ? col[e + 1] : 0);
     for (long long e = tail0; e < nnz; ++e)
-      check_pair(off, n, nnz, bits, bad, ctr, e, col[e], e + 1 < nnz ? col[e + 1] : 0);
+      check_pair(off, n, nnz, bits, bad, any_bad, ctr, e, col[e], e + 1 < nnz ? col[e + 1] : 0);
   }
   const int4* cq = reinterpret_cast<const int4*>(col + head);
   const long long warp = tid >> 5;
@@ -824,10 +836,10 @@ __global__ void __launch_bounds__(256) sorted_check_kernel(const long long* __re
         // four increasing pairs need no row bounds: only a quad with a
         // descent (a row start, or a row out of order) is checked pair by pair
         if (!(v[u].x < v[u].y && v[u].y < v[u].z && v[u].z < v[u].w && (v[u].w < nx || e + 4 >= nnz))) {
-          check_order(off, n, nnz, bits, bad, e, v[u].x, v[u].y);
-          check_order(off, n, nnz, bits, bad, e + 1, v[u].y, v[u].z);
-          check_order(off, n, nnz, bits, bad, e + 2, v[u].z, v[u].w);
-          check_order(off, n, nnz, bits, bad, e + 3, v[u].w, nx);
+          check_order(off, n, nnz, bits, bad, any_bad, e, v[u].x, v[u].y);
+          check_order(off, n, nnz, bits, bad, any_bad, e + 1, v[u].y, v[u].z);
+          check_order(off, n, nnz, bits, bad, any_bad, e + 2, v[u].z, v[u].w);
+          check_order(off, n, nnz, bits, bad, any_bad, e + 3, v[u].w, nx);
         }
       }
     }
@@ -864,7 +876,7 @@ cudaError_t launch_row_check(const long long* off, long long n, const int* col, 
   const int g = 8 * di.sm_count;
   cudaMemsetAsync(bits, 0, sizeof(unsigned) * (size_t)((nnz >> 5) + 1), s);
   rowstart_kernel<<<g, 256, 0, s>>>(off, n, bits);
-  if (nnz > 0) sorted_check_kernel<<<g, 256, 0, s>>>(off, n, col, nnz, bits, bad, ctr);
+  if (nnz > 0) sorted_check_kernel<<<g, 256, 0, s>>>(off, n, col, 0, nnz, bits, bad, nullptr, ctr);
   count_launches(nnz > 0 ? 2 : 1);
   return cudaGetLastError();
 }
@@ -882,33 +894,6 @@ cudaError_t launch_ident_stream(const long long* off, long long n, const int* co
 // Pieces of the first two sweeps while the columns are still arriving
 // (gsl_gsllpa_host): the rows are cut into chunks at row boundaries, and a
 // chunk's columns are checked and its rows swept as soon as it has landed.
-
-// Strict-increase and range check of the entries [e0, e1) of a chunk that
-// ends at a row boundary (so e1 starts a row or is nnz): the same verdicts
-// as sorted_check_kernel on those entries.  Every flagged row also raises
-// *any_bad.
-__global__ void __launch_bounds__(256) sorted_check_range_kernel(const long long* __restrict__ off, long long n,
-                                                                  const int* __restrict__ col, long long nnz,
-                                                                  long long e0, long long e1,
-                                                                  const unsigned* __restrict__ bits,
-                                                                  unsigned char* __restrict__ bad, unsigned* any_bad,
-                                                                  Counters* ctr) {
-  const unsigned long long pol = policy_evict_first();
-  for (long long e = e0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int je = ld_stream(col + e, pol);
-    if ((unsigned)je >= (unsigned)n) raise_err(&ctr->err, ERRBIT_INVALID);
-    const long long f = e + 1;
-    if (f < e1 && ((__ldg(bits + (f >> 5)) >> (f & 31)) & 1u) == 0) {
-      const int jn = ld_stream(col + f, pol);
-      if (!(je < jn)) {
-        bad[row_of(off, n, e)] = 1;
-        if (__ldcg(any_bad) == 0) atomicOr(any_bad, 1u);
-      }
-    }
-  }
-  (void)nnz;
-}
 
 // All-active binning of the rows [v0, v1) (sweep 2 runs on every vertex):
 // appended to their class regions as bin_kernel does.
@@ -970,11 +955,9 @@ cudaError_t launch_rowstart(const long long* off, long long n, unsigned* bits, l
 cudaError_t launch_chunk_check(const long long* off, long long n, const int* col, long long nnz, long long e0,
                                long long e1, const unsigned* bits, unsigned char* bad, unsigned* any_bad,
                                Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
+  (void)nnz;
   if (e1 <= e0) return cudaSuccess;
-  long long blocks = (e1 - e0 + 255) / 256;
-  const long long cap = 8ll * di.sm_count;
-  sorted_check_range_kernel<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(off, n, col, nnz, e0, e1, bits, bad,
-                                                                               any_bad, ctr);
+  sorted_check_kernel<<<8 * di.sm_count, 256, 0, s>>>(off, n, col, e0, e1, bits, bad, any_bad, ctr);
   count_launches(1);
   return cudaGetLastError();
 }

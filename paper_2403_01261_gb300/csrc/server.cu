@@ -50,6 +50,7 @@ struct Request {
   bool done = false;
   clk::time_point t_submit, t_start, t_done;
   int64_t batch_graphs = 0;
+  float h2d_ms = 0.f, compute_ms = 0.f, d2h_ms = 0.f;
 };
 
 struct Slot {
@@ -63,7 +64,20 @@ struct Slot {
   int* lab_h = nullptr;          // pinned labels
   std::vector<int64_t> vptr;
   std::vector<int32_t> iters;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // copies in, kernels, copy out
 };
+
+// Device time of a batch's phases from the slot's events (after its stream
+// has been synchronised); zeros when an event query fails.
+void phase_times(Slot& sl, float* h2d, float* comp, float* d2h) {
+  *h2d = *comp = *d2h = 0.f;
+  if (cudaEventElapsedTime(h2d, sl.ev[0], sl.ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(comp, sl.ev[1], sl.ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(d2h, sl.ev[2], sl.ev[3]) != cudaSuccess) {
+    cudaGetLastError();
+    *h2d = *comp = *d2h = 0.f;
+  }
+}
 
 }  // namespace
 
@@ -130,20 +144,25 @@ void worker_loop(gsl_server* S, int w) {
     if (G == 1 && batch[0]->nnz >= SOLO_ENTRIES) {
       Request* r = batch[0];
       gsl_stats st{};
+      cudaEventRecord(sl.ev[0], s);
       if (cudaMemcpyAsync(sl.off, r->offsets, sizeof(int64_t) * (size_t)(r->n + 1), cudaMemcpyHostToDevice, s) !=
               cudaSuccess ||
           cudaMemcpyAsync(sl.col, r->cols, sizeof(int32_t) * (size_t)r->nnz, cudaMemcpyHostToDevice, s) != cudaSuccess)
         rc = GSL_ERR_CUDA;
+      cudaEventRecord(sl.ev[1], s);
       gsl_csr csr{r->n, r->nnz, reinterpret_cast<const int64_t*>(sl.off), sl.col};
       if (rc == GSL_OK)
         rc = gsl_gsllpa(sl.ctx, &csr, nullptr, S->cfg.tolerance, S->cfg.max_iters, S->cfg.mode, sl.lab, &st, s);
+      cudaEventRecord(sl.ev[2], s);
       if (rc == GSL_OK &&
           (cudaMemcpyAsync(sl.lab_h, sl.lab, sizeof(int32_t) * (size_t)r->n, cudaMemcpyDeviceToHost, s) !=
                cudaSuccess ||
-           cudaStreamSynchronize(s) != cudaSuccess))
+           cudaEventRecord(sl.ev[3], s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
         rc = GSL_ERR_CUDA;
       if (rc != GSL_OK) cudaGetLastError();
       const auto t_done = clk::now();
+      float h2d = 0.f, comp = 0.f, d2h = 0.f;
+      if (rc == GSL_OK) phase_times(sl, &h2d, &comp, &d2h);
       {
         std::lock_guard<std::mutex> lk(S->mu);
         r->status = rc;
@@ -154,6 +173,9 @@ void worker_loop(gsl_server* S, int w) {
         r->t_start = t_start;
         r->t_done = t_done;
         r->batch_graphs = 1;
+        r->h2d_ms = h2d;
+        r->compute_ms = comp;
+        r->d2h_ms = d2h;
         r->done = true;
       }
       S->cv_done.notify_all();
@@ -164,6 +186,7 @@ void worker_loop(gsl_server* S, int w) {
       continue;
     }
     // pack: copy every solo CSR to its place, then shift offsets and columns
+    cudaEventRecord(sl.ev[0], s);
     for (int k = 0; k < G && rc == GSL_OK; ++k) {
       Request* r = batch[k];
       if (r->n > 0 &&
@@ -191,18 +214,22 @@ void worker_loop(gsl_server* S, int w) {
       if (cudaGetLastError() != cudaSuccess) rc = GSL_ERR_CUDA;
     }
     const int64_t n = sl.vptr[G], nnz = eptr[G];
+    cudaEventRecord(sl.ev[1], s);
     if (rc == GSL_OK) {
       gsl_csr csr{n, nnz, reinterpret_cast<const int64_t*>(sl.off), sl.col};
       sl.iters.assign(G, 0);
       rc = gsl_gsllpa_batch(sl.ctx, &csr, G, sl.vptr.data(), nullptr, S->cfg.tolerance, S->cfg.max_iters,
                             S->cfg.mode, sl.lab, sl.iters.data(), nullptr, s);
     }
+    cudaEventRecord(sl.ev[2], s);
     if (rc == GSL_OK && n > 0 &&
         (cudaMemcpyAsync(sl.lab_h, sl.lab, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaStreamSynchronize(s) != cudaSuccess))
+         cudaEventRecord(sl.ev[3], s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
       rc = GSL_ERR_CUDA;
     if (rc != GSL_OK) cudaGetLastError();
     const auto t_done = clk::now();
+    float h2d = 0.f, comp = 0.f, d2h = 0.f;
+    if (rc == GSL_OK && n > 0) phase_times(sl, &h2d, &comp, &d2h);
     {
       std::lock_guard<std::mutex> lk(S->mu);
       for (int k = 0; k < G; ++k) {
@@ -215,6 +242,9 @@ void worker_loop(gsl_server* S, int w) {
         r->t_start = t_start;
         r->t_done = t_done;
         r->batch_graphs = G;
+        r->h2d_ms = h2d;
+        r->compute_ms = comp;
+        r->d2h_ms = d2h;
         r->done = true;
       }
     }
@@ -228,6 +258,8 @@ void worker_loop(gsl_server* S, int w) {
 
 void free_slot(Slot& sl) {
   if (sl.ctx) gsl_ctx_destroy(sl.ctx);
+  for (auto& e : sl.ev)
+    if (e) cudaEventDestroy(e);
   void* d[] = {sl.off, sl.col, sl.lab, sl.bases};
   for (void* p : d)
     if (p) cudaFree(p);
@@ -278,6 +310,7 @@ int gsl_server_create(gsl_server** out, const gsl_server_config* cfg) {
     ok = ok && cudaMalloc(&sl.bases, sizeof(long long) * (size_t)(2 * (maxg + 1))) == cudaSuccess;
     ok = ok && cudaMallocHost(&sl.bases_h, sizeof(long long) * (size_t)(2 * (maxg + 1))) == cudaSuccess;
     ok = ok && cudaMallocHost(&sl.lab_h, sizeof(int) * (size_t)std::max<int64_t>(S->cap_v, 1)) == cudaSuccess;
+    for (auto& e : sl.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (ok) gsl_ctx_set_batch_mode(sl.ctx, 0);   // batches change shape every time: launch directly
   }
   if (!ok) {
@@ -339,6 +372,9 @@ int gsl_server_wait(gsl_server* S, int64_t id, int32_t* labels_out, gsl_request_
     info->queue_ms = std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count();
     info->service_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_start).count();
     info->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    info->h2d_ms = r->h2d_ms;
+    info->compute_ms = r->compute_ms;
+    info->d2h_ms = r->d2h_ms;
   }
   delete r;
   return rc;
