@@ -296,7 +296,7 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 // labels are merged with __match_any_sync (label_group) and only the lowest
 // lane of each group inserts.  Returns true (warp-uniform) once more than `limit`
 // distinct labels have been inserted: the table is then abandoned.
-template <bool WEIGHTED, bool ASYNC, bool GLOBAL, bool SPREAD = false>
+template <bool WEIGHTED, bool ASYNC, bool GLOBAL, bool SPREAD = false, bool LEAN_OK = false>
 __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, const int* cp, const int* wp,
                                          const int* lp, int d,
                                          SlotTable tab, unsigned cap, unsigned limit, const Pol& pol,
@@ -305,17 +305,34 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
   // three rounds in flight: labels of round r+1 and columns of round r+2
   // are requested before round r is hashed
   int jn[4], wn[4], ln[4], lw[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, 32 * u + lane, pol, jn[u], wn[u]);
+  // sweep 2's loads and CAS-first inserts (sweep_device.cuh): class 7 only;
+  // on class 6's short rows they measured slower (R-MAT 25: 9.2 -> 9.5 ms)
+  constexpr bool LEAN = SPREAD && !WEIGHTED && LEAN_OK;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    check_same_graph(a, v, jn[u]);
+    if (LEAN) {
+      jn[u] = spread_col(a, cp, d, 32 * u + lane, pol);
+      wn[u] = 1;
+    } else {
+      load_entry<WEIGHTED>(a, cp, wp, d, 32 * u + lane, pol, jn[u], wn[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (!LEAN) check_same_graph(a, v, jn[u]);
     if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-    ln[u] = entry_label<ASYNC>(a, lp, 32 * u + lane, jn[u], v, pol);
+    ln[u] = LEAN ? spread_label(a, jn[u], v, pol) : entry_label<ASYNC>(a, lp, 32 * u + lane, jn[u], v, pol);
     lw[u] = wn[u];
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, 128 + 32 * u + lane, pol, jn[u], wn[u]);
+  for (int u = 0; u < 4; ++u) {
+    if (LEAN) {
+      jn[u] = spread_col(a, cp, d, 128 + 32 * u + lane, pol);
+      wn[u] = 1;
+    } else {
+      load_entry<WEIGHTED>(a, cp, wp, d, 128 + 32 * u + lane, pol, jn[u], wn[u]);
+    }
+  }
   for (unsigned k = lane; k < cap; k += 32) {
     tab.keys[k] = EMPTY32;
     tab.sums[k] = 0;
@@ -332,13 +349,21 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
     if (e0 + 128 < d) {   // warp-uniform
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        check_same_graph(a, v, jn[u]);
+        if (!LEAN) check_same_graph(a, v, jn[u]);
         if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-        ln[u] = entry_label<ASYNC>(a, lp, e0 + 128 + 32 * u + lane, jn[u], v, pol);
+        ln[u] = LEAN ? spread_label(a, jn[u], v, pol)
+                     : entry_label<ASYNC>(a, lp, e0 + 128 + 32 * u + lane, jn[u], v, pol);
         lw[u] = wn[u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, e0 + 256 + 32 * u + lane, pol, jn[u], wn[u]);
+      for (int u = 0; u < 4; ++u) {
+        if (LEAN) {
+          jn[u] = spread_col(a, cp, d, e0 + 256 + 32 * u + lane, pol);
+          wn[u] = 1;
+        } else {
+          load_entry<WEIGHTED>(a, cp, wp, d, e0 + 256 + 32 * u + lane, pol, jn[u], wn[u]);
+        }
+      }
     }
     if (!WEIGHTED && !SPREAD) {
       // entries carrying the vertex's own label are counted in registers,
@@ -369,7 +394,9 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
                                   : (WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m));
         bool created = false;
         if (l[u] >= 0 && (SPREAD || (m & lanemask_lt()) == 0)) {
-          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
+          const unsigned sum = (LEAN && !GLOBAL)
+                                   ? slot_add_cas(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap)
+                                   : slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
           const unsigned long long k = pack_key(sum, l[u]);
           best = k > best ? k : best;
         }
@@ -433,14 +460,14 @@ __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(Swee
       const unsigned limit = (!SPILL || cap >= want) ? 0xFFFFFFFFu : cap / 4 * 3 - 128;
       unsigned own_sum = 0;
       const int* lp = a.lg ? a.lg + s : nullptr;
-      if (warp_row<WEIGHTED, ASYNC, false, SPREAD>(a, v, old, cp, wp, lp, d, tab, cap, limit, pol, best, wsum,
-                                                   own_sum) &&
+      if (warp_row<WEIGHTED, ASYNC, false, SPREAD, SPILL>(a, v, old, cp, wp, lp, d, tab, cap, limit, pol, best, wsum,
+                                                          own_sum) &&
           SPILL) {
         best = 0;
         wsum = 0;
         own_sum = 0;
-        warp_row<WEIGHTED, ASYNC, true, SPREAD>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, best, wsum,
-                                                own_sum);
+        warp_row<WEIGHTED, ASYNC, true, SPREAD, SPILL>(a, v, old, cp, wp, lp, d, gtab, want, 0xFFFFFFFFu, pol, best,
+                                                       wsum, own_sum);
       }
       __syncwarp();
       if (own_sum) {   // own_sum is warp-uniform
@@ -1027,11 +1054,11 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
     GSL_LAUNCH_GROUP(32, 5)
 #undef GSL_LAUNCH_GROUP
     case CLS_WARP_S:
-      if (!A && a.spread) launch_warp_class<W, A, TW_SMALL, false, true>(a, CLS_WARP_S, t, di, s);
+      if (!A && a.spread && !a.lg) launch_warp_class<W, A, TW_SMALL, false, true>(a, CLS_WARP_S, t, di, s);
       else launch_warp_class<W, A, TW_SMALL, false, false>(a, CLS_WARP_S, t, di, s);
       break;
     case CLS_WARP_L:
-      if (!A && a.spread) launch_warp_class<W, A, TW_LARGE, true, true>(a, CLS_WARP_L, t, di, s);
+      if (!A && a.spread && !a.lg) launch_warp_class<W, A, TW_LARGE, true, true>(a, CLS_WARP_L, t, di, s);
       else launch_warp_class<W, A, TW_LARGE, true, false>(a, CLS_WARP_L, t, di, s);
       break;
     case CLS_BLOCK:
@@ -1039,7 +1066,7 @@ cudaError_t launch_sweep_t(const SweepArgs& a, int cls, const Tuning& t, const D
       const size_t smem = (size_t)t.blk_slots * sizeof(unsigned long long);
       const int grid = (int)block_grid_size(t, di);
       const int gth = cls == CLS_HUB ? a.gthresh : 0;
-      if (!A && a.spread) {
+      if (!A && a.spread && !a.lg) {
         raise_smem_limit((const void*)sweep_block_kernel<W, A, true>, smem);
         sweep_block_kernel<W, A, true><<<grid, t.blk_block, smem, s>>>(a, cls, (unsigned)t.blk_slots, gth);
       } else {

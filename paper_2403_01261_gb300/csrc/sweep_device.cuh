@@ -148,6 +148,35 @@ __device__ __forceinline__ unsigned slot_add(SlotTable t, unsigned cap, unsigned
   return 0;
 }
 
+// Shared-table insert that probes by compare-and-swap: one atomic per probe
+// tells claimed (EMPTY), found (the label) or taken (probe on).
+__device__ __forceinline__ unsigned slot_add_cas(SlotTable t, unsigned cap, unsigned lbl, unsigned c, bool& created,
+                                                 int* err, int probe_cap) {
+  unsigned h = __umulhi(hash32(lbl), cap);
+  for (int p = 0; p < probe_cap; ++p) {
+    const unsigned k = atomicCAS(t.keys + h, EMPTY32, lbl);
+    if (k == EMPTY32 || k == lbl) {
+      created = k == EMPTY32;
+      return atomicAdd(t.sums + h, c) + c;
+    }
+    if (++h == cap) h = 0;
+  }
+  raise_err(err, ERRBIT_TIMEOUT);
+  return 0;
+}
+
+// Sweep 2's entry load and label: columns were range-checked in sweep 1 (a
+// bad one failed the call there), so an out-of-range column is only
+// clamped away (memory safety for the batched loop, which reads errors at
+// the end); no pre-gathered labels or identity labelling in sweep 2.
+__device__ __forceinline__ int spread_col(const SweepArgs& a, const int* cp, int d, int e, const Pol& pol) {
+  const int j = e < d ? ld_stream(cp + e, pol.stream) : -1;
+  return (unsigned)j < (unsigned)a.n ? j : -1;
+}
+__device__ __forceinline__ int spread_label(const SweepArgs& a, int j, int v, const Pol& pol) {
+  return (j < 0 || j == v) ? -1 : ld_label_ro(a.prev + j, pol.label);
+}
+
 // Lanes of a warp's chunk holding label l, merged so that one insert per
 // distinct label reaches the table.  When the labels read are nearly all
 // distinct (a.spread) the match costs more than it merges: every lane is
@@ -249,17 +278,24 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
   unsigned long long best = 0, wsum = 0;
   unsigned own_sum = 0;
   int jn[4], wn[4], ln[4], lw[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, cb + u * cu, pol, jn[u], wn[u]);
+  constexpr bool LEAN = SPREAD && !WEIGHTED;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    check_same_graph(a, v, jn[u]);
+    if (LEAN) { jn[u] = spread_col(a, cp, d, cb + u * cu, pol); wn[u] = 1; }
+    else load_entry<WEIGHTED>(a, cp, wp, d, cb + u * cu, pol, jn[u], wn[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (!LEAN) check_same_graph(a, v, jn[u]);
     if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-    ln[u] = entry_label<ASYNC>(a, lp, cb + u * cu, jn[u], v, pol);
+    ln[u] = LEAN ? spread_label(a, jn[u], v, pol) : entry_label<ASYNC>(a, lp, cb + u * cu, jn[u], v, pol);
     lw[u] = wn[u];
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, step + cb + u * cu, pol, jn[u], wn[u]);
+  for (int u = 0; u < 4; ++u) {
+    if (LEAN) { jn[u] = spread_col(a, cp, d, step + cb + u * cu, pol); wn[u] = 1; }
+    else load_entry<WEIGHTED>(a, cp, wp, d, step + cb + u * cu, pol, jn[u], wn[u]);
+  }
   for (unsigned k = threadIdx.x; k < cap; k += blockDim.x) {
     tab.keys[k] = EMPTY32;
     tab.sums[k] = 0;
@@ -284,13 +320,16 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
     if (r0 + step < d) {   // block-uniform
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        check_same_graph(a, v, jn[u]);
+        if (!LEAN) check_same_graph(a, v, jn[u]);
         if (jn[u] >= 0) wsum += (unsigned long long)wn[u];
-        ln[u] = entry_label<ASYNC>(a, lp, r0 + step + cb + u * cu, jn[u], v, pol);
+        ln[u] = LEAN ? spread_label(a, jn[u], v, pol) : entry_label<ASYNC>(a, lp, r0 + step + cb + u * cu, jn[u], v, pol);
         lw[u] = wn[u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) load_entry<WEIGHTED>(a, cp, wp, d, r0 + 2 * step + cb + u * cu, pol, jn[u], wn[u]);
+      for (int u = 0; u < 4; ++u) {
+        if (LEAN) { jn[u] = spread_col(a, cp, d, r0 + 2 * step + cb + u * cu, pol); wn[u] = 1; }
+        else load_entry<WEIGHTED>(a, cp, wp, d, r0 + 2 * step + cb + u * cu, pol, jn[u], wn[u]);
+      }
     }
     const bool counted = !GLOBAL && limit != 0xFFFFFFFFu;
     if (counted && __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sh.ovf[par] : 0, 0)) break;   // warp-uniform
@@ -310,7 +349,9 @@ __device__ __forceinline__ int block_row(const SweepArgs& a, int v, int own, con
                                   : (WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m));
         bool created = false;
         if (l[u] >= 0 && (SPREAD || (m & lanemask_lt()) == 0)) {
-          const unsigned sum = slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
+          const unsigned sum = (LEAN && !GLOBAL)
+                                   ? slot_add_cas(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap)
+                                   : slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
           const unsigned long long k = pack_key(sum, l[u]);
           best = k > best ? k : best;
         }
