@@ -305,9 +305,11 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
   // three rounds in flight: labels of round r+1 and columns of round r+2
   // are requested before round r is hashed
   int jn[4], wn[4], ln[4], lw[4];
-  // sweep 2's loads and CAS-first inserts (sweep_device.cuh): class 7 only;
-  // on class 6's short rows they measured slower (R-MAT 25: 9.2 -> 9.5 ms)
-  constexpr bool LEAN = SPREAD && !WEIGHTED && LEAN_OK;
+  // sweep 2's lean loads (sweep_device.cuh) in classes 6 and 7 (class 6:
+  // 9.1 -> 8.5 ms per step on R-MAT 25); the compare-and-swap-first insert
+  // in class 7 only (on class 6's short rows it measured 9.2 -> 9.5 ms)
+  constexpr bool LEAN = SPREAD && !WEIGHTED;
+  constexpr bool LEAN_CAS = LEAN && LEAN_OK;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     if (LEAN) {
@@ -394,7 +396,7 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
                                   : (WEIGHTED ? __reduce_add_sync(m, (unsigned)w[u]) : (unsigned)__popc(m));
         bool created = false;
         if (l[u] >= 0 && (SPREAD || (m & lanemask_lt()) == 0)) {
-          const unsigned sum = (LEAN && !GLOBAL)
+          const unsigned sum = (LEAN_CAS && !GLOBAL)
                                    ? slot_add_cas(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap)
                                    : slot_add<GLOBAL>(tab, cap, (unsigned)l[u], c, created, &a.ctr->err, a.probe_cap);
           const unsigned long long k = pack_key(sum, l[u]);
