@@ -179,13 +179,16 @@ __global__ void init_labels_kernel(const int* __restrict__ init, int* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Classes 0..5: G lanes per vertex, 32/G vertices per warp per step.  Eight
-// 256-thread blocks per SM (32 registers, no spills): the kernel waits on
-// its label gathers, and full occupancy hides them better than the six
-// blocks 37 registers allow (R-MAT 25: classes 3..4 to 9..16, 2.42 -> 2.15 ms
-// per step).
+// Classes 0..5: G lanes per vertex, 32/G vertices per warp per step.  A row
+// costs a chain of dependent loads (worklist entry, offsets, column, label),
+// so the rows of later steps are fetched ahead: with GROUP_STAGES = 2 the
+// worklist entry two steps ahead and the offsets one step ahead, with 3 also
+// the column one step ahead (and everything one step earlier).
+constexpr int GROUP_STAGES = 2;
+constexpr int GROUP_MIN_BLOCKS = 8;   // 256-thread blocks per SM
+
 template <int G, bool WEIGHTED, bool ASYNC>
-__global__ void __launch_bounds__(256, 8) sweep_group_kernel(SweepArgs a, int cls) {
+__global__ void __launch_bounds__(256, GROUP_MIN_BLOCKS) sweep_group_kernel(SweepArgs a, int cls) {
   if (stopped(a)) return;
   const unsigned cnt = a.ctr->cls_count[cls];
   const int* __restrict__ work = a.work + a.ctr->cls_start[cls];
@@ -197,25 +200,51 @@ __global__ void __launch_bounds__(256, 8) sweep_group_kernel(SweepArgs a, int cl
   constexpr int PER_WARP = 32 / G;
   const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  unsigned long long my_dn = 0, my_scan = 0;
-  for (long long wb = warp_id * PER_WARP; wb < (long long)cnt; wb += nwarps * PER_WARP) {
-    const long long item = wb + lane / G;
-    const bool has = item < (long long)cnt;
-    int v = 0;
-    long long s = 0;
-    int d = 0;
-    if (has) {
-      v = work[item];
-      s = a.off[v];
-      d = (int)(a.off[v + 1] - s);
+  const long long stride = nwarps * PER_WARP;
+  // this lane group's row in the step whose first item is `it`: its vertex,
+  // or -1 past the worklist (then nothing of the row is read)
+  auto vertex_at = [&](long long it) -> int { return it < (long long)cnt ? work[it] : -1; };
+  auto row_of = [&](int u, long long& rs, int& rd) {
+    rs = 0;
+    rd = 0;
+    if (u >= 0) {
+      rs = a.off[u];
+      rd = (int)(a.off[u + 1] - rs);
     }
-    int j, wt;
+  };
+  const long long item0 = warp_id * PER_WARP + lane / G;
+  int v = vertex_at(item0), vn = vertex_at(item0 + stride), vnn = -1;
+  long long s, sn = 0;
+  int d, dn = 0, j = -1, wt = 0;
+  row_of(v, s, d);
+  if (GROUP_STAGES >= 3) {
     load_entry<WEIGHTED>(a, a.col + s, a.w + s, d, gl, pol, j, wt);
-    check_same_graph(a, v, j);
+    row_of(vn, sn, dn);
+    vnn = vertex_at(item0 + 2 * stride);
+  }
+  unsigned long long my_dn = 0, my_scan = 0;
+  for (long long wb = warp_id * PER_WARP; wb < (long long)cnt; wb += stride) {
+    const long long item = wb + lane / G;
+    // fetch ahead
+    int jn = -1, wtn = 0, vf;
+    long long sf;
+    int df;
+    if (GROUP_STAGES >= 3) {
+      vf = vertex_at(item + 3 * stride);
+      row_of(vnn, sf, df);
+      load_entry<WEIGHTED>(a, a.col + sn, a.w + sn, dn, gl, pol, jn, wtn);
+    } else {
+      vf = vertex_at(item + 2 * stride);
+      row_of(vn, sf, df);
+      load_entry<WEIGHTED>(a, a.col + s, a.w + s, d, gl, pol, j, wt);
+    }
+    const bool has = v >= 0;
+    const int vv = has ? v : 0;
+    check_same_graph(a, vv, j);
     const bool nb = j >= 0;
-    const bool valid = nb && j != v;       // scanCommunities skips j == i
-    const int lbl = entry_label<ASYNC>(a, a.lg ? a.lg + s : nullptr, gl, j, v, pol);
-    const int old = (has && gl == 0) ? own_label<ASYNC>(a, v) : 0;
+    const bool valid = nb && j != vv;       // scanCommunities skips j == i
+    const int lbl = entry_label<ASYNC>(a, a.lg ? a.lg + s : nullptr, gl, j, vv, pol);
+    const int old = (has && gl == 0) ? own_label<ASYNC>(a, vv) : 0;
     if (WEIGHTED && a.check) {
       unsigned long long ws = nb ? (unsigned long long)wt : 0ull;
 #pragma unroll
@@ -232,8 +261,8 @@ __global__ void __launch_bounds__(256, 8) sweep_group_kernel(SweepArgs a, int cl
     if (has && gl == 0) {
       const int nl = mc ? (int)~binv : old;
       changed = nl != old;
-      store_label<ASYNC>(a, v, nl, changed);
-      if (changed) count_graph_change(a, v);
+      store_label<ASYNC>(a, vv, nl, changed);
+      if (changed) count_graph_change(a, vv);
       my_scan += (unsigned long long)d;
       my_dn += changed ? 1ull : 0ull;
     }
@@ -241,8 +270,14 @@ __global__ void __launch_bounds__(256, 8) sweep_group_kernel(SweepArgs a, int cl
       const unsigned chm = __ballot_sync(FULL, changed);
       if ((chm >> gbase) & 1u) {
         if (nb) a.fnext[j] = 1;
-        if (!ASYNC && gl == 0) a.fnext[v] = 1;
+        if (!ASYNC && gl == 0) a.fnext[vv] = 1;
       }
+    }
+    if (GROUP_STAGES >= 3) {
+      v = vn; s = sn; d = dn; j = jn; wt = wtn;
+      vn = vnn; sn = sf; dn = df; vnn = vf;
+    } else {
+      v = vn; s = sf; d = df; vn = vf;
     }
   }
   flush_counters(a.ctr, cls, my_dn, my_scan);
@@ -415,8 +450,9 @@ __device__ __forceinline__ bool warp_row(const SweepArgs& a, int v, int own, con
 // 7's 8 KB tables allow three).
 // With SPILL, a vertex whose labels overflow the shared table is redone in
 // the warp's region of the global fallback tables (2 * warp_max slots);
-// without it the class bound guarantees 2 d <= TW.  The next vertex's
-// worklist entry and offsets are loaded while the current one is processed.
+// without it the class bound guarantees 2 d <= TW.  The worklist entry of
+// the row after next and the offsets of the next row are loaded while the
+// current one is processed.
 template <bool WEIGHTED, bool ASYNC, int TW, bool SPILL, bool SPREAD = false>
 __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(SweepArgs a, int cls) {
   if (stopped(a)) return;
@@ -431,23 +467,25 @@ __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(Swee
   const Pol pol = make_pol();
   unsigned long long my_dn = 0, my_scan = 0;
   long long item = warp_id;
-  int vn = 0;
+  int vn = 0, vnn = 0;
   long long sn = 0, en = 0;
   if (item < (long long)cnt) {
     vn = work[item];
     sn = a.off[vn];
     en = a.off[vn + 1];
   }
+  if (item + nwarps < (long long)cnt) vnn = work[item + nwarps];
   while (item < (long long)cnt) {
     const int v = vn;
     const long long s = sn;
     const int d = (int)(en - sn);
     const long long next_item = item + nwarps;
-    if (next_item < (long long)cnt) {
-      vn = work[next_item];
+    if (next_item < (long long)cnt) {   // its worklist entry came one row earlier
+      vn = vnn;
       sn = a.off[vn];
       en = a.off[vn + 1];
     }
+    if (next_item + nwarps < (long long)cnt) vnn = work[next_item + nwarps];
     const int old = own_label<ASYNC>(a, v);
     const int* cp = a.col + s;
     const int* wp = a.w + s;
