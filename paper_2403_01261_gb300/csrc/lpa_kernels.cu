@@ -325,6 +325,73 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 
 // ---------------------------------------------------------------------------
 
+// Rows of 33..SORT_MAX entries, unit weights: one warp sorts the row's
+// labels in registers instead of hashing them.  Lane l holds entries l and
+// 32 + l (key i = r * 32 + l); a bitonic network of 21 compare-exchange
+// steps (shuffles for partners in other lanes, one in-register step for
+// partner i ^ 32) sorts the 64 keys ascending, with absent entries (past
+// the row end, out of range, the vertex itself) as 0xFFFFFFFF at the end.
+// Equal labels then form runs: a run's length is the label's count, and
+// the largest packed key (count, ~label) over the run starts is Eq. 2's
+// argmax with ties to the smallest label, the same as the table's.  No
+// shared memory, no atomics.  Returns the lane's partial key (0: none).
+constexpr int SORT_MAX = 64;
+
+template <bool ASYNC>
+__device__ __forceinline__ unsigned long long warp_sort_row(const SweepArgs& a, int v, const int* cp, const int* lp,
+                                                            int d, const Pol& pol) {
+  const int lane = threadIdx.x & 31;
+  unsigned x[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    int j, wt;
+    load_entry<false>(a, cp, nullptr, d, r * 32 + lane, pol, j, wt);
+    check_same_graph(a, v, j);
+    const int l = entry_label<ASYNC>(a, lp, r * 32 + lane, j, v, pol);
+    x[r] = l >= 0 ? (unsigned)l : 0xFFFFFFFFu;
+  }
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {   // partner i ^ 32: the lane's other key (k = 64: ascending)
+        const unsigned lo = min(x[0], x[1]), hi = max(x[0], x[1]);
+        x[0] = lo;
+        x[1] = hi;
+      } else {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const unsigned y = __shfl_xor_sync(FULL, x[r], j);
+          const bool ascending = (((r * 32 + lane) & k) == 0);
+          const bool keep_min = ((lane & j) == 0) == ascending;
+          x[r] = keep_min ? min(x[r], y) : max(x[r], y);
+        }
+      }
+    }
+  }
+  // run starts: key i differs from key i - 1
+  const unsigned p0 = __shfl_up_sync(FULL, x[0], 1);
+  unsigned p1 = __shfl_up_sync(FULL, x[1], 1);
+  const unsigned last0 = __shfl_sync(FULL, x[0], 31);
+  if (lane == 0) p1 = last0;
+  const bool s0 = lane == 0 || x[0] != p0, s1 = x[1] != p1;
+  const unsigned long long starts =
+      (unsigned long long)__ballot_sync(FULL, s0) | ((unsigned long long)__ballot_sync(FULL, s1) << 32);
+  unsigned long long best = 0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const bool st = r == 0 ? s0 : s1;
+    if (st && x[r] != 0xFFFFFFFFu) {
+      const int i = r * 32 + lane;
+      const unsigned long long above = i < 63 ? starts & ~((2ull << i) - 1ull) : 0ull;
+      const int next = above ? __ffsll((long long)above) - 1 : 64;
+      const unsigned long long key = pack_key((unsigned)(next - i), (int)x[r]);
+      best = key > best ? key : best;
+    }
+  }
+  return best;
+}
+
 // One warp aggregates the row (cp, wp, d) of vertex v into `tab` (cap
 // slots).  Four 32-entry chunks are loaded (columns, then labels) before any
 // is hashed, so each lane keeps eight loads in flight.  Within a chunk equal
@@ -492,6 +559,10 @@ __global__ void __launch_bounds__(256, TW <= 512 ? 4 : 3) sweep_warp_kernel(Swee
     unsigned long long best = 0, wsum = 0;
     bool done = false;
     if (a.ident && !ASYNC) done = __all_sync(FULL, ident_sorted_pass<WEIGHTED>(a, v, s, d, lane, 32, pol, best, wsum));
+    if (!done && !WEIGHTED && d <= SORT_MAX) {   // warp-uniform
+      best = warp_sort_row<ASYNC>(a, v, cp, a.lg ? a.lg + s : nullptr, d, pol);
+      done = true;
+    }
     if (!done) {
       best = 0;
       wsum = 0;
