@@ -431,6 +431,49 @@ def _giant_hubs(seed=4):
     return I.csr_from_pairs(n, np.concatenate(u), np.concatenate(v), name="sbm100k-giant-hubs")
 
 
+def _rows_33_64(seed=11, n=3000):
+    """Random graph whose rows hold 33..64 entries almost everywhere (each
+    vertex picks 24 neighbours), plus a vertex of exactly 64 and one of
+    exactly 33 entries, and self-loops on every 7th vertex (a row entry that
+    Eq. 2 skips)."""
+    rng = np.random.default_rng(seed)
+    edges = set()
+    for u in range(n):
+        for v in rng.choice(n, 24, replace=False):
+            if u != int(v):
+                edges.add((min(u, int(v)), max(u, int(v))))
+    m = n
+    for k, deg in ((0, 64), (1, 33)):
+        for v in rng.choice(n, deg, replace=False):
+            edges.add((int(v), m + k))
+    edges = sorted(edges) + [(v, v) for v in range(0, n, 7)]
+    return I.from_edges(n + 2, edges, name="rows33-64")
+
+
+def test_rows_of_33_to_64_entries(ctx, small_ctx):
+    """The warp's register sort (rows of 33..64 entries, unit weights)
+    against the oracle: one sweep from labels drawn from 8 values (many
+    ties) and from all vertex ids, full synchronous runs, and the
+    asynchronous invariants."""
+    g = _rows_33_64()
+    d = np.diff(g.offsets)
+    assert (d == 33).any() and (d == 64).any()
+    assert ((d >= 33) & (d <= 64)).mean() > 0.9
+    off, col, _ = dev(g)
+    rng = np.random.default_rng(4)
+    for c in (ctx, small_ctx):
+        for hi in (8, g.n):
+            prev = rng.integers(0, hi, g.n).astype(np.int32)
+            got = c.lpa(off, col, labels_init=torch.from_numpy(prev).to(DEV), tolerance=0.0, max_iters=1)
+            assert np.array_equal(got.cpu().numpy(), O.sync_sweep(g, prev)[0]), hi
+        got, st = c.lpa(off, col, tolerance=0.0, max_iters=8, stats=True)
+        want, t, dn = O.lpa_sync(g, 0.0, 8)
+        assert st["iterations"] == t and st["changed"] == dn[:t].tolist()
+        assert np.array_equal(got.cpu().numpy(), want)
+        lab = c.gsllpa(off, col, mode=1).cpu().numpy()
+        assert (lab <= np.arange(g.n)).all() and np.array_equal(lab[lab], lab) and O.disconnected(g, lab)[0] == 0
+
+
 @pytest.mark.parametrize("clu", [None, 0, 36_000])
 @pytest.mark.parametrize("tuning", [None, (1024, 4096), (256, 8192), (32, 48)])
 @pytest.mark.parametrize("w", [False, True])
