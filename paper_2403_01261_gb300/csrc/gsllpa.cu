@@ -135,6 +135,14 @@ namespace {
 // int64_t is `long` on LP64 Linux; the kernels take `long long`.
 inline const long long* OFF(const gsl_csr* g) { return reinterpret_cast<const long long*>(g->offsets); }
 
+// Single-graph sweeps: from this sweep on, the own-label majority filter
+// takes the rows of class 6 too, once most of them keep their label (R-MAT
+// 25, ms per step: from sweep 4 51.3 -> 50.6; from sweep 3 no gain, as
+// sweep 3's class-6 rows mostly change and the filter's pass over them is
+// then repeated by the warp kernel).  The batched loop keeps the filter on
+// classes 7 and 8: there it cost 10 % on planted-partition graphs.
+constexpr int FILTER6_FROM = 4;
+
 int fail(gsl_ctx* c, int code, const char* fmt, ...) {
   if (c) {
     char buf[512];
@@ -433,6 +441,9 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
     const bool filter = !a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
     if (filter)
       if (int r = grow(c, c->work2, c->cap_work2, n)) return r;
+    // from FILTER6_FROM on the filter takes class 6 (rows of 33..warp_small
+    // entries) as well
+    const int filter_from = (filter && t >= FILTER6_FROM) ? CLS_WARP_S : CLS_WARP_L;
     // An asynchronous sweep runs its frontier in two phases chosen by a hash
     // of the vertex id and the sweep number, the second reading the labels
     // the first wrote: neighbours that would update at the same moment every
@@ -447,16 +458,16 @@ int run_lpa(gsl_ctx* c, const gsl_csr* g, const int32_t* weights, const int32_t*
                       nullptr, nullptr, async_mode ? ph : -1, (unsigned)t));
         prof_end(c, pe, SL_BIN, s, 1);
       }
-      SweepArgs af = a;   // classes 7 and 8 after the filter read its worklist
+      SweepArgs af = a;   // the filtered classes read the filter's worklist
       if (filter) {
         const int pe = prof_begin(c, s);
-        CK(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, s));
+        CK(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, s, filter_from));
         prof_end(c, pe, SL_FILTER, s, 2);
         af.work = c->work2;
       }
       for (int k = NCLASS - 1; k >= 0; --k) {   // the longest rows first
         const int pe = prof_begin(c, s);
-        if (k == CLS_WARP_L || k == CLS_BLOCK) {
+        if (k == CLS_WARP_L || k == CLS_BLOCK || (k == CLS_WARP_S && filter_from == CLS_WARP_S)) {
           CK(launch_sweep_class(af, k, weights != nullptr, async_mode, c->tune, c->di, s));
           prof_end(c, pe, SL_SWEEP0 + k, s, 1);
         } else if (k == CLS_HUB && c->hub_ready) {

@@ -85,14 +85,14 @@ void count_launches(long long k);   // process-wide tally of kernels this librar
 // valid); thread-safe.
 cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 long long launches_total();
-// Own-label majority filter over classes 7 and 8: settled rows keep their
-// label; the others go to `out` (n ints, class regions as in the worklist)
-// and become the class counts of the table kernels, which must then read
-// `out` as their worklist.
-// The class counts of classes 7-8 become the rows a filter passed on.
-cudaError_t launch_filter_counts(Counters* ctr, const int* stop, cudaStream_t s);
+// Own-label majority filter over classes first_cls..8 (first_cls 6 or 7):
+// settled rows keep their label; the others go to `out` (n ints, class
+// regions as in the worklist) and become the class counts of the warp and
+// block kernels, which must then read `out` as their worklist.
+// The class counts of classes first_cls..8 become the rows a filter passed on.
+cudaError_t launch_filter_counts(Counters* ctr, const int* stop, cudaStream_t s, int first_cls = CLS_WARP_L);
 cudaError_t launch_majority_filter(const SweepArgs& a, int* out, bool weighted, bool async_mode,
-                                   const DeviceInfo& di, cudaStream_t s);
+                                   const DeviceInfo& di, cudaStream_t s, int first_cls = CLS_WARP_L);
 // Edge-parallel label gather for a synchronous sweep: lg[e] = prev[col[e]]
 // for every CSR entry (-1 for an out-of-range column).
 cudaError_t launch_pregather(const int* col, long long nnz, const int* prev, long long n, int* lg,

@@ -767,19 +767,20 @@ __device__ __forceinline__ int filter_row(const SweepArgs& a, int v, int own, co
 // Counters::uns_count; filter_counts_kernel then makes those the class
 // counts for the table kernels.
 template <bool WEIGHTED, bool ASYNC>
-__global__ void __launch_bounds__(256, 6) majority_filter_kernel(SweepArgs a, int* __restrict__ out) {
+__global__ void __launch_bounds__(256, 6) majority_filter_kernel(SweepArgs a, int* __restrict__ out, int first_cls) {
   if (stopped(a)) return;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const Pol pol = make_pol();
-  const long long c7 = a.ctr->cls_count[CLS_WARP_L];
-  const long long total = c7 + a.ctr->cls_count[CLS_BLOCK];
+  const long long c6 = first_cls <= CLS_WARP_S ? a.ctr->cls_count[CLS_WARP_S] : 0;
+  const long long c67 = c6 + a.ctr->cls_count[CLS_WARP_L];
+  const long long total = c67 + a.ctr->cls_count[CLS_BLOCK];
   unsigned long long my_scan = 0, my_settled = 0;
   for (long long i = warp; i < total; i += nwarps) {
-    const int cls = i < c7 ? CLS_WARP_L : CLS_BLOCK;
+    const int cls = i < c6 ? CLS_WARP_S : (i < c67 ? CLS_WARP_L : CLS_BLOCK);
     const long long start = a.ctr->cls_start[cls];
-    const int v = a.work[start + (i < c7 ? i : i - c7)];
+    const int v = a.work[start + (i - (i < c6 ? 0 : (i < c67 ? c6 : c67)))];
     const long long s = a.off[v];
     const int d = (int)(a.off[v + 1] - s);
     const int old = own_label<ASYNC>(a, v);
@@ -810,28 +811,28 @@ __global__ void __launch_bounds__(256, 6) majority_filter_kernel(SweepArgs a, in
   }
 }
 
-__global__ void filter_counts_kernel(Counters* ctr, const int* stop) {
+__global__ void filter_counts_kernel(Counters* ctr, const int* stop, int first_cls) {
   if (stop && *(volatile const int*)stop) return;
-  for (int k = CLS_WARP_L; k <= CLS_BLOCK; ++k) ctr->cls_count[k] = ctr->uns_count[k];
+  for (int k = first_cls; k <= CLS_BLOCK; ++k) ctr->cls_count[k] = ctr->uns_count[k];
 }
 
-cudaError_t launch_filter_counts(Counters* ctr, const int* stop, cudaStream_t s) {
-  filter_counts_kernel<<<1, 1, 0, s>>>(ctr, stop);
+cudaError_t launch_filter_counts(Counters* ctr, const int* stop, cudaStream_t s, int first_cls) {
+  filter_counts_kernel<<<1, 1, 0, s>>>(ctr, stop, first_cls);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_majority_filter(const SweepArgs& a, int* out, bool weighted, bool async_mode,
-                                   const DeviceInfo& di, cudaStream_t s) {
+                                   const DeviceInfo& di, cudaStream_t s, int first_cls) {
   const int grid = 16 * di.sm_count;
   if (weighted) {
-    if (async_mode) majority_filter_kernel<true, true><<<grid, 256, 0, s>>>(a, out);
-    else majority_filter_kernel<true, false><<<grid, 256, 0, s>>>(a, out);
+    if (async_mode) majority_filter_kernel<true, true><<<grid, 256, 0, s>>>(a, out, first_cls);
+    else majority_filter_kernel<true, false><<<grid, 256, 0, s>>>(a, out, first_cls);
   } else {
-    if (async_mode) majority_filter_kernel<false, true><<<grid, 256, 0, s>>>(a, out);
-    else majority_filter_kernel<false, false><<<grid, 256, 0, s>>>(a, out);
+    if (async_mode) majority_filter_kernel<false, true><<<grid, 256, 0, s>>>(a, out, first_cls);
+    else majority_filter_kernel<false, false><<<grid, 256, 0, s>>>(a, out, first_cls);
   }
-  filter_counts_kernel<<<1, 1, 0, s>>>(a.ctr, a.stop);
+  filter_counts_kernel<<<1, 1, 0, s>>>(a.ctr, a.stop, first_cls);
   count_launches(2);
   return cudaGetLastError();
 }
