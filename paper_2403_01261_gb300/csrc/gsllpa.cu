@@ -139,9 +139,11 @@ inline const long long* OFF(const gsl_csr* g) { return reinterpret_cast<const lo
 // takes the rows of class 6 too, once most of them keep their label (R-MAT
 // 25, ms per step: from sweep 4 51.3 -> 50.6; from sweep 3 no gain, as
 // sweep 3's class-6 rows mostly change and the filter's pass over them is
-// then repeated by the warp kernel).  The batched loop keeps the filter on
-// classes 7 and 8: there it cost 10 % on planted-partition graphs.
+// then repeated by the warp kernel).  The batched loop's planted-partition
+// graphs settle later (4096-graph batch, ms per step: none 459.8, from
+// sweep 4 500.5, from sweep 6 454.1).
 constexpr int FILTER6_FROM = 4;
+constexpr int BATCH_FILTER6_FROM = 6;
 
 int fail(gsl_ctx* c, int code, const char* fmt, ...) {
   if (c) {
@@ -853,6 +855,7 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
     a.check = t == 1 ? 1 : 0;
     a.mark = t >= 2 ? 1 : 0;   // sweep 2 runs on all vertices, later ones on the marked frontier
     const bool filter = !a.ident && !a.check && (c->tune.majority == 2 || (c->tune.majority == 1 && t >= 3));
+    const int filter_from = (filter && t >= BATCH_FILTER6_FROM) ? CLS_WARP_S : CLS_WARP_L;
     a.gthresh = (t == 2 && !async_mode) ? 3 * c->tune.blk_slots : 0;
     a.spread = (t == 2 && !async_mode) ? 1 : 0;
     const int phases = async_mode ? 2 : 1;   // asynchronous sweeps in two phases, as in run_lpa
@@ -865,14 +868,14 @@ cudaError_t enqueue_batch_sweeps(gsl_ctx* c, const gsl_csr* g, int num_graphs, c
       SweepArgs af = a;
       if (filter) {
         pe = prof ? prof_begin(c, cs) : -1;
-        ck(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, cs));
+        ck(launch_majority_filter(a, c->work2, weights != nullptr, async_mode, c->di, cs, filter_from));
         if (prof) prof_end(c, pe, SL_FILTER, cs, 2);
         af.work = c->work2;
       }
       for (int k = 0; k < NCLASS; ++k) {
         pe = prof ? prof_begin(c, cs) : -1;
-        ck(launch_sweep_class(k == CLS_WARP_L || k == CLS_BLOCK ? af : a, k, weights != nullptr, async_mode, c->tune,
-                              c->di, cs));
+        const bool filtered = k == CLS_WARP_L || k == CLS_BLOCK || (k == CLS_WARP_S && filter_from == CLS_WARP_S);
+        ck(launch_sweep_class(filtered ? af : a, k, weights != nullptr, async_mode, c->tune, c->di, cs));
         if (prof) prof_end(c, pe, SL_SWEEP0 + k, cs, 1);
       }
     }
