@@ -181,10 +181,10 @@ __global__ void init_labels_kernel(const int* __restrict__ init, int* __restrict
 // ---------------------------------------------------------------------------
 // Classes 0..5: G lanes per vertex, 32/G vertices per warp per step.  A row
 // costs a chain of dependent loads (worklist entry, offsets, column, label),
-// so the rows of later steps are fetched ahead: with GROUP_STAGES = 2 the
-// worklist entry two steps ahead and the offsets one step ahead, with 3 also
-// the column one step ahead (and everything one step earlier).
-constexpr int GROUP_STAGES = 2;
+// so the rows of later steps are fetched ahead: the worklist entry two steps
+// ahead, the offsets one step ahead.  Eight 256-thread blocks per SM (32
+// registers): the kernel waits on its label gathers, and full occupancy
+// hides them better than fewer blocks with the column fetched ahead too.
 constexpr int GROUP_MIN_BLOCKS = 8;   // 256-thread blocks per SM
 
 template <int G, bool WEIGHTED, bool ASYNC>
@@ -213,31 +213,20 @@ __global__ void __launch_bounds__(256, GROUP_MIN_BLOCKS) sweep_group_kernel(Swee
     }
   };
   const long long item0 = warp_id * PER_WARP + lane / G;
-  int v = vertex_at(item0), vn = vertex_at(item0 + stride), vnn = -1;
-  long long s, sn = 0;
-  int d, dn = 0, j = -1, wt = 0;
+  int v = vertex_at(item0), vn = vertex_at(item0 + stride);
+  long long s;
+  int d;
   row_of(v, s, d);
-  if (GROUP_STAGES >= 3) {
-    load_entry<WEIGHTED>(a, a.col + s, a.w + s, d, gl, pol, j, wt);
-    row_of(vn, sn, dn);
-    vnn = vertex_at(item0 + 2 * stride);
-  }
   unsigned long long my_dn = 0, my_scan = 0;
   for (long long wb = warp_id * PER_WARP; wb < (long long)cnt; wb += stride) {
     const long long item = wb + lane / G;
-    // fetch ahead
-    int jn = -1, wtn = 0, vf;
+    // fetch ahead: the worklist entry two steps on, the offsets of the next step
+    const int vf = vertex_at(item + 2 * stride);
     long long sf;
     int df;
-    if (GROUP_STAGES >= 3) {
-      vf = vertex_at(item + 3 * stride);
-      row_of(vnn, sf, df);
-      load_entry<WEIGHTED>(a, a.col + sn, a.w + sn, dn, gl, pol, jn, wtn);
-    } else {
-      vf = vertex_at(item + 2 * stride);
-      row_of(vn, sf, df);
-      load_entry<WEIGHTED>(a, a.col + s, a.w + s, d, gl, pol, j, wt);
-    }
+    row_of(vn, sf, df);
+    int j, wt;
+    load_entry<WEIGHTED>(a, a.col + s, a.w + s, d, gl, pol, j, wt);
     const bool has = v >= 0;
     const int vv = has ? v : 0;
     check_same_graph(a, vv, j);
@@ -273,12 +262,10 @@ __global__ void __launch_bounds__(256, GROUP_MIN_BLOCKS) sweep_group_kernel(Swee
         if (!ASYNC && gl == 0) a.fnext[vv] = 1;
       }
     }
-    if (GROUP_STAGES >= 3) {
-      v = vn; s = sn; d = dn; j = jn; wt = wtn;
-      vn = vnn; sn = sf; dn = df; vnn = vf;
-    } else {
-      v = vn; s = sf; d = df; vn = vf;
-    }
+    v = vn;
+    s = sf;
+    d = df;
+    vn = vf;
   }
   flush_counters(a.ctr, cls, my_dn, my_scan);
 }
@@ -326,24 +313,26 @@ __device__ __forceinline__ bool ident_sorted_pass(const SweepArgs& a, int v, lon
 // ---------------------------------------------------------------------------
 
 // Rows of 33..SORT_MAX entries, unit weights: one warp sorts the row's
-// labels in registers instead of hashing them.  Lane l holds entries l and
-// 32 + l (key i = r * 32 + l); a bitonic network of 21 compare-exchange
-// steps (shuffles for partners in other lanes, one in-register step for
-// partner i ^ 32) sorts the 64 keys ascending, with absent entries (past
-// the row end, out of range, the vertex itself) as 0xFFFFFFFF at the end.
-// Equal labels then form runs: a run's length is the label's count, and
-// the largest packed key (count, ~label) over the run starts is Eq. 2's
-// argmax with ties to the smallest label, the same as the table's.  No
-// shared memory, no atomics.  Returns the lane's partial key (0: none).
-constexpr int SORT_MAX = 64;
+// labels in registers instead of hashing them.  Lane l holds entries
+// r * 32 + l (r < SORT_K); a bitonic network (shuffles for partners in other
+// lanes, in-register steps for partners r ^ (j / 32)) sorts the keys
+// ascending, with absent entries (past the row end, out of range, the vertex
+// itself) as 0xFFFFFFFF at the end.  Equal labels then form runs: a run's
+// length is the label's count, and the largest packed key (count, ~label)
+// over the run starts is Eq. 2's argmax with ties to the smallest label, the
+// same as the table's.  No shared memory, no atomics.  Returns the lane's
+// partial key (0: none).
+constexpr int SORT_K = 2;
+constexpr int SORT_MAX = 32 * SORT_K;
 
 template <bool ASYNC>
 __device__ __forceinline__ unsigned long long warp_sort_row(const SweepArgs& a, int v, const int* cp, const int* lp,
                                                             int d, const Pol& pol) {
+  constexpr int N = 32 * SORT_K;
   const int lane = threadIdx.x & 31;
-  unsigned x[2];
+  unsigned x[SORT_K];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < SORT_K; ++r) {
     int j, wt;
     load_entry<false>(a, cp, nullptr, d, r * 32 + lane, pol, j, wt);
     check_same_graph(a, v, j);
@@ -351,16 +340,23 @@ __device__ __forceinline__ unsigned long long warp_sort_row(const SweepArgs& a, 
     x[r] = l >= 0 ? (unsigned)l : 0xFFFFFFFFu;
   }
 #pragma unroll
-  for (int k = 2; k <= 64; k <<= 1) {
+  for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j == 32) {   // partner i ^ 32: the lane's other key (k = 64: ascending)
-        const unsigned lo = min(x[0], x[1]), hi = max(x[0], x[1]);
-        x[0] = lo;
-        x[1] = hi;
+      if (j >= 32) {   // partner r ^ (j / 32): the same lane's other keys
+#pragma unroll
+        for (int r = 0; r < SORT_K; ++r) {
+          const int h = r ^ (j >> 5);
+          if (r < h) {
+            const bool ascending = (((r * 32 + lane) & k) == 0);
+            const unsigned lo = min(x[r], x[h]), hi = max(x[r], x[h]);
+            x[r] = ascending ? lo : hi;
+            x[h] = ascending ? hi : lo;
+          }
+        }
       } else {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < SORT_K; ++r) {
           const unsigned y = __shfl_xor_sync(FULL, x[r], j);
           const bool ascending = (((r * 32 + lane) & k) == 0);
           const bool keep_min = ((lane & j) == 0) == ascending;
@@ -370,22 +366,30 @@ __device__ __forceinline__ unsigned long long warp_sort_row(const SweepArgs& a, 
     }
   }
   // run starts: key i differs from key i - 1
-  const unsigned p0 = __shfl_up_sync(FULL, x[0], 1);
-  unsigned p1 = __shfl_up_sync(FULL, x[1], 1);
-  const unsigned last0 = __shfl_sync(FULL, x[0], 31);
-  if (lane == 0) p1 = last0;
-  const bool s0 = lane == 0 || x[0] != p0, s1 = x[1] != p1;
-  const unsigned long long starts =
-      (unsigned long long)__ballot_sync(FULL, s0) | ((unsigned long long)__ballot_sync(FULL, s1) << 32);
+  unsigned w[SORT_K];
+  bool st[SORT_K];
+#pragma unroll
+  for (int r = 0; r < SORT_K; ++r) {
+    unsigned p = __shfl_up_sync(FULL, x[r], 1);
+    const unsigned last = __shfl_sync(FULL, x[r > 0 ? r - 1 : 0], 31);
+    if (lane == 0 && r > 0) p = last;
+    st[r] = (lane == 0 && r == 0) || x[r] != p;
+    w[r] = __ballot_sync(FULL, st[r]);
+  }
   unsigned long long best = 0;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const bool st = r == 0 ? s0 : s1;
-    if (st && x[r] != 0xFFFFFFFFu) {
-      const int i = r * 32 + lane;
-      const unsigned long long above = i < 63 ? starts & ~((2ull << i) - 1ull) : 0ull;
-      const int next = above ? __ffsll((long long)above) - 1 : 64;
-      const unsigned long long key = pack_key((unsigned)(next - i), (int)x[r]);
+  for (int r = 0; r < SORT_K; ++r) {
+    if (st[r] && x[r] != 0xFFFFFFFFu) {
+      const unsigned above = lane < 31 ? w[r] & ~((2u << lane) - 1u) : 0u;
+      int next = N;
+      if (above) {
+        next = r * 32 + __ffs((int)above) - 1;
+      } else {
+#pragma unroll
+        for (int q = SORT_K - 1; q > r; --q)
+          if (w[q]) next = q * 32 + __ffs((int)w[q]) - 1;
+      }
+      const unsigned long long key = pack_key((unsigned)(next - (r * 32 + lane)), (int)x[r]);
       best = key > best ? key : best;
     }
   }
