@@ -244,6 +244,30 @@ def test_host_overlap_matches_oracle(graph, ctx, gpu_lib, pinned):
         assert st["active"] == st_dev["active"] and st["communities"] == st_dev["communities"], (tol, iters)
 
 
+def test_host_overlap_skewed_chunks(gpu_lib):
+    """Chunk bounds of the overlapped host path when rows are very unequal:
+    a star whose centre holds most entries (several chunk targets fall in
+    one row), isolated vertices at both ends of the id range, a graph with
+    fewer entries than chunks, and one edge.  Labels, sweep counts and
+    per-sweep dN equal the oracle's."""
+    rng = np.random.default_rng(8)
+    n = 5000
+    edges = [(0, v) for v in range(1, 4000)]                          # the centre's row: most entries
+    edges += [(int(a), int(b)) for a, b in rng.integers(1, 4000, (1500, 2)) if a != b]
+    star = I.from_edges(n, sorted({(min(a, b), max(a, b)) for a, b in edges}), name="star-isolated-tail")
+    graphs = [star, I.from_edges(6, [(1, 2), (2, 3)], name="tiny"), I.from_edges(2, [(0, 1)], name="one-edge"),
+              I.path(9)]
+    c = gpu_lib.Context(0)
+    c.set_host_overlap(1)
+    for g in graphs:
+        off, col = torch.from_numpy(g.offsets).pin_memory(), torch.from_numpy(g.cols).pin_memory()
+        for tol, iters in [(0.05, 20), (0.0, 2)]:
+            want_lpa, t, dn = O.lpa_sync(g, tol, iters)
+            got, st = c.gsllpa_host(off, col, tolerance=tol, max_iters=iters, stats=True)
+            assert np.array_equal(got.numpy(), O.split_bfs(g, want_lpa)), (g.name, tol, iters)
+            assert st["iterations"] == t and st["changed"] == dn.tolist(), (g.name, tol, iters)
+
+
 def test_host_overlap_falls_back_on_unsorted_rows(gpu_lib):
     """Rows that are not strictly increasing (shuffled, with repeated
     entries) break the first sweep's premise: the overlapped host path
