@@ -51,17 +51,30 @@ __global__ void class_histogram_kernel(const long long* __restrict__ off, long l
   __syncthreads();
   long long lmax = 0;
   int lbad = 0;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    const long long s = off[v], e = off[v + 1];
-    if (s < 0 || e < s || e > nnz) { lbad |= ERRBIT_INVALID; continue; }
-    const long long d = e - s;
-    if (d >= (1ll << 31)) { lbad |= ERRBIT_OVERFLOW; continue; }
-    lmax = d > lmax ? d : lmax;
-    const int c = degree_class(d, cb.warp_small, cb.warp_max, cb.blk_max);
-    if (c >= 0) atomicAdd(&hist[c], 1ull);
-    if (c == CLS_HUB) atomicAdd(&hub_e, (unsigned long long)d);
-    if (v == 0 && s != 0) lbad |= ERRBIT_INVALID;
-    if (v == n - 1 && e != nnz) lbad |= ERRBIT_INVALID;
+  // whole warps step together (the bound is warp-uniform), so that equal
+  // classes are counted with one shared atomic per warp
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long v0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+  for (long long w = v0; w < n; w += stride) {
+    const long long v = w + (threadIdx.x & 31);
+    int c = -1;
+    if (v < n) {
+      const long long s = off[v], e = off[v + 1];
+      if (s < 0 || e < s || e > nnz) {
+        lbad |= ERRBIT_INVALID;
+      } else if (e - s >= (1ll << 31)) {
+        lbad |= ERRBIT_OVERFLOW;
+      } else {
+        const long long d = e - s;
+        lmax = d > lmax ? d : lmax;
+        c = degree_class(d, cb.warp_small, cb.warp_max, cb.blk_max);
+        if (c == CLS_HUB) atomicAdd(&hub_e, (unsigned long long)d);
+      }
+      if (v == 0 && s != 0) lbad |= ERRBIT_INVALID;
+      if (v == n - 1 && e != nnz) lbad |= ERRBIT_INVALID;
+    }
+    const unsigned m = __match_any_sync(FULL, c);
+    if (c >= 0 && (m & lanemask_lt()) == 0) atomicAdd(&hist[c], (unsigned long long)__popc(m));
   }
   if (lmax) atomicMax(&maxd, lmax);
   if (lbad) atomicOr(&bad, lbad);

@@ -270,18 +270,32 @@ constexpr int RN_THREADS = 256;
 constexpr int RN_ITEMS = 8;
 constexpr long long RN_TILE = (long long)RN_THREADS * RN_ITEMS;
 
+// Representatives per tile of RN_TILE vertices (thread t of the block takes
+// vertices t * RN_ITEMS .. + RN_ITEMS - 1 of the tile, as rn_rank_kernel
+// does).  A thread's eight labels are read as two 16-byte loads where the
+// array is 16-byte aligned and the eight lie inside it.
 __global__ void __launch_bounds__(RN_THREADS) rn_count_kernel(const int* __restrict__ rep, long long n,
                                                                unsigned long long* __restrict__ block_sums) {
-  __shared__ unsigned long long acc;
+  static_assert(RN_ITEMS == 8, "two 16-byte loads per thread");
+  __shared__ unsigned acc;
   if (threadIdx.x == 0) acc = 0;
   __syncthreads();
-  const long long t0 = (long long)blockIdx.x * RN_TILE;
+  const long long v0 = (long long)blockIdx.x * RN_TILE + (long long)threadIdx.x * RN_ITEMS;
   unsigned c = 0;
-  for (int k = 0; k < RN_ITEMS; ++k) {
-    const long long v = t0 + (long long)threadIdx.x * RN_ITEMS + k;
-    if (v < n && rep[v] == (int)v) ++c;
+  if ((reinterpret_cast<uintptr_t>(rep) & 15) == 0 && v0 + RN_ITEMS <= n) {
+    const int4 x = __ldg(reinterpret_cast<const int4*>(rep + v0));
+    const int4 y = __ldg(reinterpret_cast<const int4*>(rep + v0 + 4));
+    const int v = (int)v0;
+    c = (x.x == v) + (x.y == v + 1) + (x.z == v + 2) + (x.w == v + 3) + (y.x == v + 4) + (y.y == v + 5) +
+        (y.z == v + 6) + (y.w == v + 7);
+  } else {
+    for (int k = 0; k < RN_ITEMS; ++k) {
+      const long long v = v0 + k;
+      if (v < n && rep[v] == (int)v) ++c;
+    }
   }
-  atomicAdd(&acc, (unsigned long long)c);
+  c = __reduce_add_sync(FULL, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&acc, c);
   __syncthreads();
   if (threadIdx.x == 0) block_sums[blockIdx.x] = acc;
 }
