@@ -118,9 +118,10 @@ __device__ __forceinline__ int sweep_phase(long long v, unsigned seed) {
 // PHASED is a template flag so that the one-phase binning of synchronous
 // sweeps carries no phase test.
 constexpr int BIN_ITEMS = 8;
+constexpr int BIN_BLOCKS = 6;   // resident 256-thread blocks per SM (40 registers); the grid is no larger
 
 template <bool PHASED>
-__global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ off, long long n,
+__global__ void __launch_bounds__(256, BIN_BLOCKS) bin_kernel(const long long* __restrict__ off, long long n,
                                                    unsigned char* __restrict__ fcur, int all_active, ClassBounds cb,
                                                    int* __restrict__ work, Counters* ctr, const int* __restrict__ gid,
                                                    const unsigned char* __restrict__ done, const int* stop, int phase,
@@ -154,6 +155,11 @@ __global__ void __launch_bounds__(256) bin_kernel(const long long* __restrict__ 
         if (act && gid && done[gid[v]]) act = false;   // batched: this vertex's graph has stopped
         if (act) cls[k] = degree_class(off[v + 1] - off[v], cb.warp_small, cb.warp_max, cb.blk_max);
       }
+    }
+    // every item's class is known before any is counted, so that the
+    // tile's offset loads are all in flight together
+#pragma unroll
+    for (int k = 0; k < BIN_ITEMS; ++k) {
       // one shared-memory add per class present in the warp
       const unsigned m = __match_any_sync(FULL, cls[k]);
       const int leader = __ffs(m) - 1;
@@ -1280,7 +1286,7 @@ cudaError_t launch_bin(const long long* off, long long n, unsigned char* fcur, i
   if (n <= 0) return cudaSuccess;
   const long long tile = 256ll * BIN_ITEMS;
   long long blocks = (n + tile - 1) / tile;
-  const long long cap = 8ll * di.sm_count;
+  const long long cap = (long long)BIN_BLOCKS * di.sm_count;
   const int grid = (int)(blocks < cap ? blocks : cap);
   if (phase >= 0)
     bin_kernel<true><<<grid, 256, 0, s>>>(off, n, fcur, all_active, class_bounds(t), work, ctr, gid, done, stop, phase,
