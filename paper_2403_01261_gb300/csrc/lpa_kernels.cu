@@ -1032,13 +1032,30 @@ __global__ void ident_first_kernel(const long long* __restrict__ off, long long 
   }
 }
 
+namespace {
+// One wave of 256-thread blocks of `kernel`: as many as are resident at once
+// (the streaming passes of sweep 1 use more registers than eight blocks per
+// SM allow, and a second wave would run at part of the bandwidth).
+template <typename K>
+int one_wave_grid(K kernel, const DeviceInfo& di) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 0;
+  }
+  return (per_sm < 1 ? 1 : per_sm) * di.sm_count;
+}
+}  // namespace
+
 cudaError_t launch_row_check(const long long* off, long long n, const int* col, long long nnz, unsigned* bits,
                              unsigned char* bad, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int g = 8 * di.sm_count;
+  thread_local int gc = 0;
+  if (!gc) gc = one_wave_grid(sorted_check_kernel, di);
   cudaMemsetAsync(bits, 0, sizeof(unsigned) * (size_t)((nnz >> 5) + 1), s);
   rowstart_kernel<<<g, 256, 0, s>>>(off, n, bits);
-  if (nnz > 0) sorted_check_kernel<<<g, 256, 0, s>>>(off, n, col, 0, nnz, bits, bad, nullptr, ctr);
+  if (nnz > 0) sorted_check_kernel<<<gc, 256, 0, s>>>(off, n, col, 0, nnz, bits, bad, nullptr, ctr);
   count_launches(nnz > 0 ? 2 : 1);
   return cudaGetLastError();
 }
@@ -1047,7 +1064,9 @@ cudaError_t launch_ident_stream(const long long* off, long long n, const int* co
                                 unsigned char* bad, int* next, Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (cudaError_t e = launch_row_check(off, n, col, nnz, bits, bad, ctr, di, s)) return e;
-  ident_first_kernel<<<8 * di.sm_count, 256, 0, s>>>(off, n, col, bad, next, ctr);
+  thread_local int gi = 0;
+  if (!gi) gi = one_wave_grid(ident_first_kernel, di);
+  ident_first_kernel<<<gi, 256, 0, s>>>(off, n, col, bad, next, ctr);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1119,7 +1138,9 @@ cudaError_t launch_chunk_check(const long long* off, long long n, const int* col
                                Counters* ctr, const DeviceInfo& di, cudaStream_t s) {
   (void)nnz;
   if (e1 <= e0) return cudaSuccess;
-  sorted_check_kernel<<<8 * di.sm_count, 256, 0, s>>>(off, n, col, e0, e1, bits, bad, any_bad, ctr);
+  thread_local int gc = 0;
+  if (!gc) gc = one_wave_grid(sorted_check_kernel, di);
+  sorted_check_kernel<<<gc, 256, 0, s>>>(off, n, col, e0, e1, bits, bad, any_bad, ctr);
   count_launches(1);
   return cudaGetLastError();
 }
