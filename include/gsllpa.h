@@ -103,14 +103,15 @@ int gsl_ctx_set_tuning(gsl_ctx* ctx, int32_t warp_max, int32_t blk_max);
 int gsl_ctx_set_block_config(gsl_ctx* ctx, int32_t threads, int32_t table_slots);
 
 /* Own-label majority filter for rows of the two longest table classes
- * (degree above 256 up to blk_max; the paper has no counterpart).  Before
- * their hash tables are built, one lean warp-per-row pass sums the weight
- * of a row's entries carrying the vertex's own label; when it is more than
- * half of the row's weight (the vertex itself excluded) the own label is
- * Eq. 2's strict argmax and the row is done.  mode 0: never; 1 (default):
- * from sweep 3 on (sweep 2 reads the nearly all-distinct labels of sweep 1);
- * 2: every sweep after the first.  Labels and statistics do not depend on
- * the mode. */
+ * (degree above 256 up to blk_max; the paper has no counterpart), and also
+ * for the rows of 33..256 entries from sweep 4 on in single-graph calls and
+ * from sweep 6 on in the batched loop.  Before their hash tables are built,
+ * one lean warp-per-row pass sums the weight of a row's entries carrying
+ * the vertex's own label; when it is more than half of the row's weight
+ * (the vertex itself excluded) the own label is Eq. 2's strict argmax and
+ * the row is done.  mode 0: never; 1 (default): from sweep 3 on (sweep 2
+ * reads the nearly all-distinct labels of sweep 1); 2: every sweep after
+ * the first.  Labels and statistics do not depend on the mode. */
 int gsl_ctx_set_majority(gsl_ctx* ctx, int32_t mode);
 
 /* Two-phase synchronous sweeps (the paper has no counterpart: it is a GPU
