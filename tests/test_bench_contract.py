@@ -26,3 +26,58 @@ def test_reference_arm_json_line(tmp_path):
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def _slot(name, ms, nbytes, launches=1):
+    return {"name": name, "ms": ms, "bytes": nbytes, "launches": launches, "kernels": launches, "vertices": 0,
+            "entries": 0}
+
+
+def test_dominant_roofline_arithmetic(monkeypatch):
+    """The slot with the largest device time is the dominant one; achieved
+    = its algorithmic bytes over its time, frac = achieved / peak; slots
+    without bytes are ignored."""
+    b = _bench()
+    from paper_2403_01261_gb300 import _build
+    monkeypatch.setattr(_build, "source_hash", lambda: "no-such-hash")
+    prof = [_slot("sweep_block", 20.0, 40e9, launches=4), _slot("sweep_hub", 10.0, 50e9), _slot("idle", 30.0, 0.0)]
+    r = b.dominant_roofline(prof, (1000.0, "measured"))
+    assert r["kernel"] == "sweep_block" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 2000.0) < 1e-9 and abs(r["frac"] - 2.0) < 1e-12
+    assert r["bytes_per_launch"] == 10e9 and r["ms_per_launch"] == 5.0 and r["launches"] == 4
+    assert r["traffic"] is None and r["peak_source"] == "measured"
+    assert b.dominant_roofline([_slot("x", 0.0, 1.0)], (1.0, "fallback")) is None
+
+
+def test_roofline_traffic_only_for_the_profiled_library(monkeypatch):
+    """profiles/traffic.json is used only when its source hash is the built
+    library's; any other hash gives traffic null."""
+    b = _bench()
+    from paper_2403_01261_gb300 import _build
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    prof = [_slot("sweep_block", 10.0, 1e9)]
+    monkeypatch.setattr(_build, "source_hash", lambda: rec["source_hash"])
+    assert b.dominant_roofline(prof, (1.0, "measured"))["traffic"] == rec["per_launch"]["sweep_block"]
+    monkeypatch.setattr(_build, "source_hash", lambda: rec["source_hash"] + "x")
+    assert b.dominant_roofline(prof, (1.0, "measured"))["traffic"] is None
+
+
+def test_phase_roofline_split_and_step():
+    """The sweep phase counts every slot but the split and modularity; the
+    step counts every slot but modularity over the measured step time."""
+    b = _bench()
+    prof = [_slot("sweep_block", 4.0, 8e9), _slot("majority_filter", 6.0, 2e9), _slot("split_unionfind", 5.0, 5e9),
+            _slot("split_count_renumber", 1.0, 1e9), _slot("modularity", 2.0, 9e9)]
+    r = b.phase_roofline(prof, 100.0, steps=2, step_ms=10.0)
+    assert abs(r["sweep_phase"]["achieved"] - 1000.0) < 1e-9          # 10 GB over 10 ms
+    assert r["sweep_phase"]["bytes_per_step"] == 5e9 and r["sweep_phase"]["ms_per_step"] == 5.0
+    assert abs(r["sweep_phase"]["frac"] - 10.0) < 1e-12
+    assert abs(r["step"]["achieved"] - 800.0) < 1e-9                  # 16 GB / 2 steps over 10 ms
+    assert r["step"]["bytes_per_step"] == 8e9 and r["step"]["ms_per_step"] == 10.0
+    assert b.phase_roofline([], 1.0, steps=1, step_ms=0.0) == {}
