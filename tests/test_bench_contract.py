@@ -81,3 +81,22 @@ def test_phase_roofline_split_and_step():
     assert abs(r["step"]["achieved"] - 800.0) < 1e-9                  # 16 GB / 2 steps over 10 ms
     assert r["step"]["bytes_per_step"] == 8e9 and r["step"]["ms_per_step"] == 10.0
     assert b.phase_roofline([], 1.0, steps=1, step_ms=0.0) == {}
+
+
+def test_pack_graphs_is_the_disjoint_union():
+    """The batched workload's packing: graph k's vertices are vptr[k]..,
+    its rows and columns shifted by its vertex and entry offsets; graphs
+    with no vertex or no entry keep their place; connected components of
+    the union never cross graphs."""
+    import numpy as np
+    import inputs as I
+    b = _bench()
+    parts = [I.path(4), I.from_edges(3, [], name="empty"), I.from_edges(0, [], name="none"), I.two_cliques_bridge(5)]
+    off, col, vptr = b.pack_graphs([(g.offsets, g.cols) for g in parts])
+    assert vptr.tolist() == [0, 4, 7, 7, 17]
+    assert off.shape[0] == 18 and off[0] == 0 and off[-1] == col.shape[0] == sum(g.cols.shape[0] for g in parts)
+    for k, g in enumerate(parts):
+        v0, v1 = int(vptr[k]), int(vptr[k + 1])
+        assert np.array_equal(off[v0:v1 + 1] - off[v0], g.offsets)
+        seg = col[off[v0]:off[v1]]
+        assert np.array_equal(seg - v0, g.cols) and ((seg >= v0) & (seg < v1)).all()
